@@ -1,0 +1,398 @@
+/*
+ * CPU ORACLE for the free-hand ultrasound volume path -- TEST INFRASTRUCTURE.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py (cpu_baseline leg and the
+ * reference arm) may load this file.  The product path (the CUDA library
+ * under paper_2412_00058_gb300/) never calls it and shares no code with it.
+ *
+ * Plain, slow, obviously-correct C in FP64 / exact integers.  One function
+ * per step of the path, each following the definition it cites:
+ *
+ *   ora_frame_affine_q32   per-frame pixel->voxel affine map (Alg. 1 steps
+ *                          2, 3, 6: a pixel is carried into the reference
+ *                          frame by the tracked transform T_T^W applied after
+ *                          the image calibration), quantised to Q31.32.
+ *   ora_insert_pnn         pixel-nearest-neighbour insertion (Sec. II.C: PNN
+ *                          after Solberg et al.; every pixel goes to its
+ *                          nearest voxel, which accumulates intensity and a
+ *                          hit count).
+ *   ora_fill_pnn           normalisation (bin value = sum / count) and the
+ *                          3x3x3 hole-filling pass of PNN (Sec. II.C, PNN's
+ *                          second stage).
+ *   ora_project_u8         depth-band projection, the VPI spine view at a
+ *                          fixed depth (Sec. III.B, Fig. 6).
+ *   ora_insert_trilinear   distance-weighted (trilinear) splatting variant,
+ *   ora_fill_trilinear     its normalisation + hole fill, and
+ *   ora_project_f64        its depth-band projection, all in FP64.
+ *
+ * Where the paper is silent the reading taken is stated at the function.
+ * Build with -ffp-contract=off: the affine set-up is defined as separately
+ * rounded IEEE multiplies and adds (no fused multiply-add).
+ */
+#include "usv_oracle.h"
+
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define TWO32 4294967296.0
+
+/* Round half away from zero, exactly.  x - trunc(x) is exact in binary
+ * floating point, so the comparison with 0.5 decides the tie rule. */
+int64_t ora_round_half_away(double x)
+{
+    double t = trunc(x);
+    double r = x - t;
+    if (r >= 0.5)
+        t += 1.0;
+    else if (r <= -0.5)
+        t -= 1.0;
+    return (int64_t)t;
+}
+
+/* floor(a / b) for b > 0, written out (C division truncates toward zero). */
+static int64_t floor_div(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    if ((a % b) != 0 && a < 0)
+        q -= 1;
+    return q;
+}
+
+/* M = P * K restricted to the top three rows; every entry is the four
+ * products summed left to right, each operation rounded (no FMA). */
+static void pose_times_calib(const double P[16], const double K[16], double M[3][4])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 4; ++j) {
+            double acc = P[i * 4 + 0] * K[0 * 4 + j];
+            acc = acc + P[i * 4 + 1] * K[1 * 4 + j];
+            acc = acc + P[i * 4 + 2] * K[2 * 4 + j];
+            acc = acc + P[i * 4 + 3] * K[3 * 4 + j];
+            M[i][j] = acc;
+        }
+}
+
+/*
+ * Per-frame affine map from pixel (u, v) to continuous voxel coordinates
+ *     q(u, v) = C + u*A + v*B
+ * where the world point of the pixel is p = P K (u*sx, 0, v*sy, 1)^T
+ * (Alg. 1 steps 2-3 and 6: the image point is carried to the world by the
+ * calibration and the tracked probe pose T_T^W) and q = (p - origin)/spacing:
+ *     A_a = (M[a][0]*sx)/s_a,  B_a = (M[a][2]*sy)/s_a,  C_a = (M[a][3]-o_a)/s_a.
+ * The nine values are quantised to Q31.32 (round half away from zero of
+ * value * 2^32).  coef = {A_x,A_y,A_z, B_x,B_y,B_z, C_x,C_y,C_z}.
+ *
+ * Reading (the paper fixes no precision): the quantised map *defines* the
+ * nearest-neighbour result.  A frame is valid iff the pose's bottom row is
+ * exactly (0,0,0,1), all nine values are finite, |A_a| < 2^14, |B_a| < 2^14
+ * and |C_a| < 2^29; invalid frames are skipped.  Returns 1 if valid.
+ */
+int ora_frame_affine_q32(const double P[16], const double K[16], double sx, double sy,
+                         const double spacing[3], const double origin[3], int64_t coef[9])
+{
+    double M[3][4];
+    double A[3], B[3], C[3];
+    int ok = P[12] == 0.0 && P[13] == 0.0 && P[14] == 0.0 && P[15] == 1.0;
+    pose_times_calib(P, K, M);
+    for (int a = 0; a < 3; ++a) {
+        A[a] = (M[a][0] * sx) / spacing[a];
+        B[a] = (M[a][2] * sy) / spacing[a];
+        C[a] = (M[a][3] - origin[a]) / spacing[a];
+        if (!isfinite(A[a]) || !isfinite(B[a]) || !isfinite(C[a]))
+            ok = 0;
+        else if (fabs(A[a]) >= 16384.0 || fabs(B[a]) >= 16384.0 || fabs(C[a]) >= 536870912.0)
+            ok = 0;
+    }
+    for (int a = 0; a < 3; ++a) {
+        coef[a] = ok ? ora_round_half_away(A[a] * TWO32) : 0;
+        coef[3 + a] = ok ? ora_round_half_away(B[a] * TWO32) : 0;
+        coef[6 + a] = ok ? ora_round_half_away(C[a] * TWO32) : 0;
+    }
+    return ok;
+}
+
+/*
+ * PNN insertion (Sec. II.C).  For every pixel of every valid frame:
+ *   Q_a = C_a + u*A_a + v*B_a                (exact int64, Q31.32)
+ *   i_a = floor((Q_a + 2^31) / 2^32)        (nearest voxel; ties go up)
+ * and if 0 <= i_a < n_a on all axes, sum[i] += I(u, v) and cnt[i] += 1.
+ * Every pixel is inserted, zeros included.  Volume order [nz][ny][nx].
+ * Returns the number of frames skipped as invalid.
+ */
+int64_t ora_insert_pnn(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz,
+                       const uint8_t *images, int n, int H, int W, const double *poses,
+                       const double K[16], double sx, double sy,
+                       const double spacing[3], const double origin[3])
+{
+    int64_t skipped = 0;
+    const int64_t half = (int64_t)1 << 31;
+    const int64_t one = (int64_t)1 << 32;
+    for (int f = 0; f < n; ++f) {
+        int64_t c[9];
+        if (!ora_frame_affine_q32(poses + (size_t)f * 16, K, sx, sy, spacing, origin, c)) {
+            ++skipped;
+            continue;
+        }
+        const uint8_t *img = images + (size_t)f * H * W;
+        for (int v = 0; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                int64_t idx[3];
+                for (int a = 0; a < 3; ++a) {
+                    int64_t Q = c[6 + a] + (int64_t)u * c[a] + (int64_t)v * c[3 + a];
+                    idx[a] = floor_div(Q + half, one);
+                }
+                if (idx[0] < 0 || idx[0] >= nx || idx[1] < 0 || idx[1] >= ny || idx[2] < 0 ||
+                    idx[2] >= nz)
+                    continue;
+                size_t lin = ((size_t)idx[2] * ny + (size_t)idx[1]) * nx + (size_t)idx[0];
+                sum[lin] += img[(size_t)v * W + u];
+                cnt[lin] += 1;
+            }
+    }
+    return skipped;
+}
+
+/* round-half-up mean of integer data: floor(s/c + 1/2) = (2s + c) / (2c) */
+static uint8_t mean_u8(uint64_t s, uint64_t c)
+{
+    uint64_t q = (2 * s + c) / (2 * c);
+    return (uint8_t)(q > 255 ? 255 : q);
+}
+
+/*
+ * Normalisation and 3x3x3 hole filling for PNN (Sec. II.C: PNN's bin
+ * value is the mean of the pixels that fell into it; empty bins are then
+ * filled from their neighbourhood).  Reading: one pass that reads only the
+ * accumulators; an empty voxel takes the pooled, count-weighted mean
+ * (sum of neighbour sums over sum of neighbour counts) of its non-empty
+ * in-grid neighbours among the 26; with none it stays empty (has = 0,
+ * val = 0).  Means round half up.
+ */
+void ora_fill_pnn(const uint64_t *sum, const uint32_t *cnt, int nx, int ny, int nz,
+                  uint8_t *val, uint8_t *has)
+{
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t i = ((size_t)z * ny + y) * nx + x;
+                if (cnt[i] > 0) {
+                    val[i] = mean_u8(sum[i], cnt[i]);
+                    has[i] = 1;
+                    continue;
+                }
+                uint64_t S = 0, C = 0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (dx == 0 && dy == 0 && dz == 0)
+                                continue;
+                            int X = x + dx, Y = y + dy, Z = z + dz;
+                            if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz)
+                                continue;
+                            size_t j = ((size_t)Z * ny + Y) * nx + X;
+                            if (cnt[j] > 0) {
+                                S += sum[j];
+                                C += cnt[j];
+                            }
+                        }
+                if (C > 0) {
+                    val[i] = mean_u8(S, C);
+                    has[i] = 1;
+                } else {
+                    val[i] = 0;
+                    has[i] = 0;
+                }
+            }
+}
+
+/*
+ * Depth-band projection (the VPI view at a fixed depth, Sec. III.B).
+ * Reading: for every (x, y) the mean of the has-data voxels with z in the
+ * half-open band [lo, hi), as a float (0 where there are none); cnt gets the
+ * number of voxels averaged.
+ */
+void ora_project_u8(const uint8_t *val, const uint8_t *has, int nx, int ny, int nz, int lo,
+                    int hi, float *out, uint16_t *cnt)
+{
+    (void)nz;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            uint64_t s = 0, c = 0;
+            for (int z = lo; z < hi; ++z) {
+                size_t i = ((size_t)z * ny + y) * nx + x;
+                if (has[i]) {
+                    s += val[i];
+                    c += 1;
+                }
+            }
+            out[(size_t)y * nx + x] = c ? (float)((double)s / (double)c) : 0.0f;
+            if (cnt)
+                cnt[(size_t)y * nx + x] = (uint16_t)c;
+        }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Trilinear (distance-weighted) variant, FP64 throughout.                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * In-plane point (mm, image frame) of sample (row i, column j).
+ *   linear: (j*sx, 0, i*sy)
+ *   convex: r = r0 + i*dr, theta = -sector/2 + j*sector/(W-1);
+ *           (r sin(theta), 0, r cos(theta) - r0)   [origin at the centre of
+ *           the transducer face, z pointing into the body]
+ * Reading: the paper's 6C1 convex probe (Sec. III.A) gives no radius; r0 is
+ * a parameter and the beams are spread evenly over the sector, both ends
+ * included.
+ */
+static void sample_point(const ora_geometry *g, int W, int i, int j, double *xi, double *zi)
+{
+    if (g->convex) {
+        const double pi = 3.14159265358979323846;
+        double half = g->sector_deg * pi / 360.0;
+        double th = -half + (double)j * (2.0 * half / (double)(W - 1));
+        double r = g->r0 + (double)i * g->dr;
+        *xi = r * sin(th);
+        *zi = r * cos(th) - g->r0;
+    } else {
+        *xi = (double)j * g->sx;
+        *zi = (double)i * g->sy;
+    }
+}
+
+/*
+ * Trilinear splatting.  Each sample at continuous voxel position q spreads
+ * its intensity over the 8 voxels around it with the trilinear weights
+ * w = prod_a (1 - f_a or f_a), f = q - floor(q):  S += w*I, Wt += w.
+ * Readings: corners outside the grid are dropped without renormalising;
+ * weights below 2^-20 are dropped; a voxel is empty iff Wt == 0.  Frames are
+ * skipped when invalid: the pose's bottom row must be exactly (0,0,0,1)
+ * and, per axis, the map's values must be finite with |C_a| < 2^29 and the
+ * per-step (linear: per pixel, A_a = M[a][0]*sx/s_a, B_a = M[a][2]*sy/s_a)
+ * or per-mm (convex: M[a][0]/s_a, M[a][2]/s_a) factors below 2^14.
+ * images: uint8 (is_f32 == 0) or float32, [n][H][W].
+ */
+int64_t ora_insert_trilinear(double *S, double *Wt, int nx, int ny, int nz,
+                             const void *images, int is_f32, int n, int H, int W,
+                             const double *poses, const double K[16], const ora_geometry *g,
+                             const double spacing[3], const double origin[3])
+{
+    int64_t skipped = 0;
+    const double wmin = 1.0 / 1048576.0; /* 2^-20 */
+    for (int f = 0; f < n; ++f) {
+        const double *P = poses + (size_t)f * 16;
+        double M[3][4];
+        int ok = P[12] == 0.0 && P[13] == 0.0 && P[14] == 0.0 && P[15] == 1.0;
+        pose_times_calib(P, K, M);
+        for (int a = 0; a < 3; ++a) {
+            double A = g->convex ? M[a][0] / spacing[a] : (M[a][0] * g->sx) / spacing[a];
+            double B = g->convex ? M[a][2] / spacing[a] : (M[a][2] * g->sy) / spacing[a];
+            double C = (M[a][3] - origin[a]) / spacing[a];
+            if (!isfinite(A) || !isfinite(B) || !isfinite(C))
+                ok = 0;
+            else if (fabs(A) >= 16384.0 || fabs(B) >= 16384.0 || fabs(C) >= 536870912.0)
+                ok = 0;
+        }
+        if (!ok) {
+            ++skipped;
+            continue;
+        }
+        for (int i = 0; i < H; ++i)
+            for (int j = 0; j < W; ++j) {
+                double xi, zi, q[3], fr[3];
+                int64_t i0[3];
+                sample_point(g, W, i, j, &xi, &zi);
+                for (int a = 0; a < 3; ++a) {
+                    double p = M[a][0] * xi + M[a][2] * zi + M[a][3];
+                    q[a] = (p - origin[a]) / spacing[a];
+                    double fl = floor(q[a]);
+                    i0[a] = (int64_t)fl;
+                    fr[a] = q[a] - fl;
+                }
+                double I = is_f32 ? (double)((const float *)images)[((size_t)f * H + i) * W + j]
+                                  : (double)((const uint8_t *)images)[((size_t)f * H + i) * W + j];
+                for (int cz = 0; cz < 2; ++cz)
+                    for (int cy = 0; cy < 2; ++cy)
+                        for (int cx = 0; cx < 2; ++cx) {
+                            int64_t X = i0[0] + cx, Y = i0[1] + cy, Z = i0[2] + cz;
+                            if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz)
+                                continue;
+                            double w = (cx ? fr[0] : 1.0 - fr[0]) * (cy ? fr[1] : 1.0 - fr[1]) *
+                                       (cz ? fr[2] : 1.0 - fr[2]);
+                            if (w < wmin)
+                                continue;
+                            size_t lin = ((size_t)Z * ny + (size_t)Y) * nx + (size_t)X;
+                            S[lin] += w * I;
+                            Wt[lin] += w;
+                        }
+            }
+    }
+    return skipped;
+}
+
+/*
+ * Normalisation + 3x3x3 hole fill for the weighted variant: a voxel with
+ * Wt > 0 takes S/Wt; an empty one takes (sum of neighbour S)/(sum of
+ * neighbour Wt) over its non-empty in-grid neighbours among the 26; with
+ * none it stays empty.
+ */
+void ora_fill_trilinear(const double *S, const double *Wt, int nx, int ny, int nz, double *val,
+                        uint8_t *has)
+{
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                size_t i = ((size_t)z * ny + y) * nx + x;
+                if (Wt[i] > 0.0) {
+                    val[i] = S[i] / Wt[i];
+                    has[i] = 1;
+                    continue;
+                }
+                double SS = 0.0, WW = 0.0;
+                for (int dz = -1; dz <= 1; ++dz)
+                    for (int dy = -1; dy <= 1; ++dy)
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            if (dx == 0 && dy == 0 && dz == 0)
+                                continue;
+                            int X = x + dx, Y = y + dy, Z = z + dz;
+                            if (X < 0 || X >= nx || Y < 0 || Y >= ny || Z < 0 || Z >= nz)
+                                continue;
+                            size_t j = ((size_t)Z * ny + Y) * nx + X;
+                            if (Wt[j] > 0.0) {
+                                SS += S[j];
+                                WW += Wt[j];
+                            }
+                        }
+                if (WW > 0.0) {
+                    val[i] = SS / WW;
+                    has[i] = 1;
+                } else {
+                    val[i] = 0.0;
+                    has[i] = 0;
+                }
+            }
+}
+
+/* Depth-band mean of a real-valued volume over has-data voxels, FP64. */
+void ora_project_f64(const double *val, const uint8_t *has, int nx, int ny, int nz, int lo,
+                     int hi, double *out, uint16_t *cnt)
+{
+    (void)nz;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            double s = 0.0;
+            uint64_t c = 0;
+            for (int z = lo; z < hi; ++z) {
+                size_t i = ((size_t)z * ny + y) * nx + x;
+                if (has[i]) {
+                    s += val[i];
+                    c += 1;
+                }
+            }
+            out[(size_t)y * nx + x] = c ? s / (double)c : 0.0;
+            if (cnt)
+                cnt[(size_t)y * nx + x] = (uint16_t)c;
+        }
+}
