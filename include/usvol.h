@@ -1,0 +1,192 @@
+/*
+ * usvol -- GB300 (sm_103a) free-hand ultrasound volume reconstruction.
+ *
+ * C ABI of the data-parallel path of "Real-time volumetric free-hand
+ * ultrasound imaging for large-sized organs" (arXiv 2412.00058):
+ *
+ *   pose-tracked B-mode frames --insert--> voxel accumulators
+ *        --fill (normalise + 3x3x3 hole fill)--> voxel values + has-data mask
+ *        --project (depth band)--> coronal spine view
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Axes: x lateral, y along the spine (sweep), z depth.  Volumes are stored
+ *    C-order [nz][ny][nx] (x fastest).  Voxel (i,j,k) has its centre at
+ *    origin + (i,j,k)*spacing (mm).
+ *  - Linear-probe frame pixel (u, v) = (column, row) sits at the image-frame
+ *    point (u*sx, 0, v*sy) mm, the upper-left pixel at the origin (the
+ *    paper's Alg. 1 steps 2-3 locate frames by their upper-left pixel).
+ *    Convex frames hold pre-scan-conversion samples: row i is the radius
+ *    r = r0 + i*dr, column j the beam angle theta_j = -sector/2 +
+ *    j*sector/(W-1); the sample sits at (r sin theta, 0, r cos theta - r0).
+ *  - image_to_probe (calibration) and poses (probe->world, the paper's
+ *    T_T^W, Alg. 1) are 4x4 row-major float64 matrices; the world point of
+ *    a pixel is p = pose * image_to_probe * (x_img, 0, z_img, 1)^T.
+ *  - Every call is asynchronous on the caller's CUDA stream (`stream` is a
+ *    cudaStream_t; NULL = legacy default stream).  Device-side conditions
+ *    (skipped frames, saturated voxels) are reported by usv_status().
+ *  - Pointers named *_dev are device pointers owned by the caller; they must
+ *    stay valid until the stream has passed the call.  The library never
+ *    allocates device memory: the volume lives in caller-provided storage.
+ *  - Return value: USV_OK (0) or a negative USV_ERR_* code.  Argument errors
+ *    are detected on the host before anything is launched.
+ *  - A usv_volume is not thread-safe; use it from one host thread / stream.
+ */
+#ifndef USVOL_H
+#define USVOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define USVOL_ABI_VERSION 1
+
+/* ---- return codes ---- */
+#define USV_OK 0
+#define USV_ERR_ARG (-1)     /* bad argument (null pointer, bad size, bad matrix) */
+#define USV_ERR_RANGE (-2)   /* argument outside the supported range            */
+#define USV_ERR_CUDA (-3)    /* a CUDA runtime call failed                      */
+#define USV_ERR_TIMEOUT (-4) /* a bounded device wait ran out                   */
+#define USV_ERR_NOMEM (-5)   /* caller storage smaller than usv_volume_bytes()  */
+#define USV_ERR_UNSUPPORTED (-6) /* mode / geometry / dtype combination not built */
+
+/* ---- device status bits returned by usv_status() ---- */
+#define USV_STATUS_BAD_POSE 0x1u   /* >= 1 frame skipped: non-affine pose, NaN/Inf or out of range */
+#define USV_STATUS_SATURATED 0x2u  /* >= 1 voxel count reached 2^24 (its sum may have wrapped)     */
+#define USV_STATUS_TIMEOUT 0x4u    /* a bounded device wait gave up                                 */
+
+typedef struct usv_volume usv_volume; /* opaque, host-side handle */
+
+typedef enum {
+    USV_PNN = 0,      /* pixel nearest neighbour, exact integer sum + count (Sec. II.C) */
+    USV_TRILINEAR = 1 /* trilinear splat, FP32 weighted sum + weight                    */
+} usv_mode;
+
+typedef enum { USV_LINEAR = 0, USV_CONVEX = 1 } usv_geom;
+typedef enum { USV_U8 = 0, USV_F32 = 1 } usv_dtype;
+
+typedef struct {
+    int32_t nx, ny, nz;
+} usv_grid;
+
+typedef struct {
+    double image_to_probe[16]; /* 4x4 row-major, bottom row must be 0 0 0 1 */
+    int32_t geom;              /* usv_geom */
+    double sx_mm, sy_mm;       /* linear: lateral / axial pixel spacing      */
+    double r0_mm, dr_mm;       /* convex: first sample radius, radial step   */
+    double sector_deg;         /* convex: full sector angle (0, 180)         */
+} usv_calibration;
+
+/* ------------------------------------------------------------------------
+ * usv_volume_bytes -- device bytes a volume needs: accumulators, filled
+ * values, has-data bit mask, per-frame set-up scratch and the status word.
+ * PNN: 8 B + 1 B + 1/8 B per voxel (+ ~0.6 MB); trilinear: 8 + 4 + 1/8.
+ * Returns 0 if the grid is invalid (any n < 1, or more than 2^31-1 voxels).
+ * ---------------------------------------------------------------------- */
+size_t usv_volume_bytes(usv_grid grid, int32_t mode);
+
+/* ------------------------------------------------------------------------
+ * usv_volume_create -- bind a volume to caller-provided device storage
+ * (the paper's reconstruction volume, Sec. II.C).  `device_storage` must be
+ * 256-byte aligned and hold usv_volume_bytes(grid, mode) bytes; it stays
+ * owned by the caller and must outlive the handle.  spacing_mm > 0 and
+ * finite; origin_mm finite (centre of voxel (0,0,0)).  The accumulators are
+ * NOT cleared: call usv_volume_reset() before the first insert.
+ * Allocates only the small host-side handle.
+ * ---------------------------------------------------------------------- */
+int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double origin_mm[3],
+                      int32_t mode, void *device_storage, size_t storage_bytes,
+                      usv_volume **out);
+
+/* Frees the host handle only; the storage is the caller's. */
+int usv_volume_destroy(usv_volume *vol);
+
+/* Zero the accumulators and the status word (start of a new scan). */
+int usv_volume_reset(usv_volume *vol, void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_insert_frames -- insert n frames into the volume (Sec. II.C: PNN
+ * reconstruction of the newly acquired frames only, on top of what the
+ * volume already holds -- the paper's incremental method).
+ *   images_dev  [n][H][W] uint8 (USV_U8) or float32 (USV_F32), C-order.
+ *   poses_dev   [n][16] float64 probe->world matrices, 8-byte aligned.
+ *   cal         host struct, read during the call only.
+ * USV_PNN: every pixel goes to its nearest voxel; with the per-frame map
+ *   q(u,v) = C + u*A + v*B quantised to Q31.32 (each of the nine values
+ *   rounded half away from zero after multiplying by 2^32; the FP64 set-up
+ *   M = pose*K is summed left to right without fused multiply-add, then
+ *   A = M[:,0]*sx/s, B = M[:,2]*sy/s, C = (M[:,3]-origin)/s), the voxel is
+ *   floor((Q + 2^31) / 2^32) per axis; pixels outside the grid are dropped;
+ *   the voxel's sum += I, count += 1.  Exact and order-independent.
+ *   Needs USV_U8 and USV_LINEAR.
+ * USV_TRILINEAR: each sample spreads I over its 8 neighbouring voxels with
+ *   trilinear weights (weights < 2^-20 and out-of-grid corners dropped),
+ *   FP32 accumulation.  USV_U8 or USV_F32; USV_LINEAR or USV_CONVEX.
+ * A frame whose pose is not affine (bottom row != 0 0 0 1), not finite, or
+ * maps outside +-2^29 voxels (|A|,|B| >= 2^14 per step) is skipped and sets
+ * USV_STATUS_BAD_POSE.  Limits: 0 <= n, 1 <= H, W <= 32768.
+ * ---------------------------------------------------------------------- */
+int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                      void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_fill_holes -- normalisation + hole filling (PNN's second stage; the
+ * 3x3x3 neighbourhood is radius 1, the only radius built).  One pass that
+ * reads only the accumulators, so it can be re-run after more inserts:
+ *   count > 0 : value = mean (PNN: (2*sum + count) / (2*count), integer
+ *               round half up, uint8; trilinear: S / W in FP32);
+ *   count == 0: value = pooled mean over the non-empty in-grid neighbours
+ *               among the 26 (sum of sums / sum of counts); none -> empty.
+ * Writes the value volume and the has-data bit mask.
+ * ---------------------------------------------------------------------- */
+int usv_fill_holes(usv_volume *vol, int32_t radius, void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_project_depth_band -- the VPI spine view (Sec. III.B): for every
+ * (x, y) the mean of the filled values of the has-data voxels with
+ * z_lo <= z < z_hi (0 where there are none), one IEEE FP32 division.
+ *   out_dev    [ny][nx] float32 (required)
+ *   count_dev  [ny][nx] uint16 number of voxels averaged (may be NULL)
+ * Requires 0 <= z_lo < z_hi <= nz and z_hi - z_lo <= 65535.  Reads the
+ * output of the last usv_fill_holes().
+ * ---------------------------------------------------------------------- */
+int usv_project_depth_band(usv_volume *vol, int32_t z_lo, int32_t z_hi, float *out_dev,
+                           uint16_t *count_dev, void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_volume_read -- copy one field to caller device memory in canonical
+ * [nz][ny][nx] order (the paper saves the finished volume as slices).
+ *   USV_READ_ACCUM : PNN uint64 (low 32 bits sum, high 32 bits count);
+ *                    trilinear float32 pairs (S, W)
+ *   USV_READ_VALUES: PNN uint8; trilinear float32
+ *   USV_READ_MASK  : uint8 0/1 has-data
+ * USV_WRITE_ACCUM (usv_volume_write) loads accumulators back, e.g. to
+ * resume a saved scan bit-exactly.
+ * ---------------------------------------------------------------------- */
+#define USV_READ_ACCUM 0
+#define USV_READ_VALUES 1
+#define USV_READ_MASK 2
+int usv_volume_read(usv_volume *vol, int32_t what, void *dst_dev, void *stream);
+int usv_volume_write_accum(usv_volume *vol, const void *src_dev, void *stream);
+
+/* Synchronise `stream`, then return the device status bits (>= 0) and clear
+ * them, or a negative USV_ERR_* code. */
+int usv_status(usv_volume *vol, void *stream);
+
+/* Human-readable text for a return code. */
+const char *usv_strerror(int code);
+
+/* Text of the CUDA error behind the calling thread's last USV_ERR_CUDA. */
+const char *usv_last_cuda_error(void);
+
+/* ABI version compiled into the library (USVOL_ABI_VERSION). */
+int usv_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* USVOL_H */

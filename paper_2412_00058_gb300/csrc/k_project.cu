@@ -1,0 +1,87 @@
+// A4: depth-band projection -- the VPI spine view at a fixed depth (Sec.
+// III.B, Fig. 6: coronal images from a fixed depth of 35 or 45 mm).  For
+// every (x, y), the mean of the filled values of the has-data voxels with
+// z in [lo, hi), 0 where there are none; one IEEE FP32 division.
+//
+// GB300 design: one thread per (x, y) column marching down the band; a warp
+// reads 32 consecutive bytes of a row per plane and shares one mask word.
+// The band is a few MB, so this kernel is launch/latency-bound rather than
+// HBM-bound; it is kept separate so several bands can be projected from one
+// filled volume.
+#include "usv_internal.cuh"
+
+namespace usv {
+
+namespace {
+
+struct ProjArgs {
+    const void *val;
+    const uint32_t *mask;
+    float *out;
+    uint16_t *cnt;
+    int nx, ny, nxw, lo, hi;
+};
+
+__global__ void __launch_bounds__(256) k_project_u8(ProjArgs a)
+{
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= a.nx || y >= a.ny)
+        return;
+    const auto *val = static_cast<const uint8_t *>(a.val);
+    const size_t plane = (size_t)a.ny * a.nx, mplane = (size_t)a.ny * a.nxw;
+    const size_t i0 = (size_t)y * a.nx + x, m0 = (size_t)y * a.nxw + (x >> 5);
+    unsigned s = 0, c = 0;
+    for (int z = a.lo; z < a.hi; ++z) {
+        const unsigned bit = (__ldg(a.mask + m0 + z * mplane) >> (x & 31)) & 1u;
+        const unsigned v = __ldg(val + i0 + z * plane);
+        s += bit ? v : 0u;
+        c += bit;
+    }
+    a.out[i0] = c ? __fdiv_rn((float)s, (float)c) : 0.0f;
+    if (a.cnt)
+        a.cnt[i0] = (uint16_t)c;
+}
+
+__global__ void __launch_bounds__(256) k_project_f32(ProjArgs a)
+{
+    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
+    if (x >= a.nx || y >= a.ny)
+        return;
+    const auto *val = static_cast<const float *>(a.val);
+    const size_t plane = (size_t)a.ny * a.nx, mplane = (size_t)a.ny * a.nxw;
+    const size_t i0 = (size_t)y * a.nx + x, m0 = (size_t)y * a.nxw + (x >> 5);
+    float s = 0.0f;
+    unsigned c = 0;
+    for (int z = a.lo; z < a.hi; ++z) {
+        const unsigned bit = (__ldg(a.mask + m0 + z * mplane) >> (x & 31)) & 1u;
+        if (bit) {
+            s += __ldg(val + i0 + z * plane);
+            c += 1;
+        }
+    }
+    a.out[i0] = c ? __fdiv_rn(s, (float)c) : 0.0f;
+    if (a.cnt)
+        a.cnt[i0] = (uint16_t)c;
+}
+
+}  // namespace
+
+cudaError_t launch_project_u8(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
+                              cudaStream_t st)
+{
+    ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi};
+    dim3 grid((v.g.nx + 31) / 32, (v.g.ny + 7) / 8);
+    k_project_u8<<<grid, dim3(32, 8), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_f32(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
+                               cudaStream_t st)
+{
+    ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi};
+    dim3 grid((v.g.nx + 31) / 32, (v.g.ny + 7) / 8);
+    k_project_f32<<<grid, dim3(32, 8), 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace usv

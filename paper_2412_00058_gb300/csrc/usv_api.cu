@@ -1,0 +1,348 @@
+// The C ABI of include/usvol.h: host-side argument checks, the storage
+// layout inside caller-provided device memory, and the launches.  Nothing
+// here allocates device memory; the only host allocation is the handle.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "usv_internal.cuh"
+
+namespace usv {
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+bool grid_ok(usv_grid g)
+{
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1)
+        return false;
+    const unsigned long long n = (unsigned long long)g.nx * g.ny * g.nz;
+    return n <= 0x7FFFFFFFull;
+}
+
+bool finite3(const double *v)
+{
+    return v && std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+bool affine_ok(const double *m)
+{
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(m[i]))
+            return false;
+    return m[12] == 0.0 && m[13] == 0.0 && m[14] == 0.0 && m[15] == 1.0;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev)
+            cudaSetDevice(dev);
+        else
+            prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+thread_local const char *t_last_cuda_error = "no error";
+
+int cuda_rc(cudaError_t e)
+{
+    if (e == cudaSuccess)
+        return USV_OK;
+    t_last_cuda_error = cudaGetErrorString(e);
+    cudaGetLastError();  // clear a sticky launch error so later calls are not blamed
+    return USV_ERR_CUDA;
+}
+
+}  // namespace
+
+Layout layout_for(usv_grid g, int mode)
+{
+    Layout L{};
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t nxw = ((size_t)g.nx + 31) / 32;
+    size_t off = 0;
+    L.acc = off;
+    off += align_up(n * 8);
+    L.val = off;
+    off += align_up(n * (mode == USV_PNN ? 1 : 4));
+    L.mask = off;
+    off += align_up((size_t)g.nz * g.ny * nxw * 4);
+    L.rec = off;
+    off += align_up((size_t)kRecCap * sizeof(FrameRec));
+    L.beams = off;
+    off += align_up((size_t)kBeamCap * sizeof(double2));
+    L.status = off;
+    off += kAlign;
+    L.total = off;
+    return L;
+}
+
+}  // namespace usv
+
+using usv::Volume;
+
+extern "C" {
+
+int usv_abi_version(void) { return USVOL_ABI_VERSION; }
+
+const char *usv_last_cuda_error(void) { return usv::t_last_cuda_error; }
+
+const char *usv_strerror(int code)
+{
+    switch (code) {
+    case USV_OK: return "ok";
+    case USV_ERR_ARG: return "invalid argument";
+    case USV_ERR_RANGE: return "argument out of supported range";
+    case USV_ERR_CUDA: return "CUDA runtime error";
+    case USV_ERR_TIMEOUT: return "bounded device wait timed out";
+    case USV_ERR_NOMEM: return "device storage smaller than usv_volume_bytes()";
+    case USV_ERR_UNSUPPORTED: return "unsupported mode/geometry/dtype combination";
+    default: return "unknown usvol error";
+    }
+}
+
+size_t usv_volume_bytes(usv_grid grid, int32_t mode)
+{
+    if (!usv::grid_ok(grid) || (mode != USV_PNN && mode != USV_TRILINEAR))
+        return 0;
+    return usv::layout_for(grid, mode).total;
+}
+
+int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double origin_mm[3],
+                      int32_t mode, void *device_storage, size_t storage_bytes, usv_volume **out)
+{
+    if (!out)
+        return USV_ERR_ARG;
+    *out = nullptr;
+    if (!usv::grid_ok(grid) || (mode != USV_PNN && mode != USV_TRILINEAR))
+        return USV_ERR_ARG;
+    if (!usv::finite3(spacing_mm) || !usv::finite3(origin_mm))
+        return USV_ERR_ARG;
+    if (!(spacing_mm[0] > 0.0 && spacing_mm[1] > 0.0 && spacing_mm[2] > 0.0))
+        return USV_ERR_ARG;
+    if (!device_storage || (reinterpret_cast<uintptr_t>(device_storage) % usv::kAlign) != 0)
+        return USV_ERR_ARG;
+    const usv::Layout L = usv::layout_for(grid, mode);
+    if (storage_bytes < L.total)
+        return USV_ERR_NOMEM;
+    cudaPointerAttributes attr;
+    if (int rc = usv::cuda_rc(cudaPointerGetAttributes(&attr, device_storage)))
+        return rc;
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return USV_ERR_ARG;
+    int sms = 0;
+    if (int rc = usv::cuda_rc(
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, attr.device)))
+        return rc;
+    Volume *v = new (std::nothrow) Volume();
+    if (!v)
+        return USV_ERR_NOMEM;
+    v->g = grid;
+    for (int a = 0; a < 3; ++a) {
+        v->spacing[a] = spacing_mm[a];
+        v->origin[a] = origin_mm[a];
+    }
+    v->mode = mode;
+    v->base = static_cast<char *>(device_storage);
+    v->bytes = storage_bytes;
+    v->acc = v->base + L.acc;
+    v->val = v->base + L.val;
+    v->mask = reinterpret_cast<uint32_t *>(v->base + L.mask);
+    v->nxw = (grid.nx + 31) / 32;
+    v->rec = reinterpret_cast<usv::FrameRec *>(v->base + L.rec);
+    v->beams = reinterpret_cast<double2 *>(v->base + L.beams);
+    v->status = reinterpret_cast<uint32_t *>(v->base + L.status);
+    v->num_sms = sms;
+    v->device = attr.device;
+    *out = reinterpret_cast<usv_volume *>(v);
+    return USV_OK;
+}
+
+int usv_volume_destroy(usv_volume *vol)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    delete reinterpret_cast<Volume *>(vol);
+    return USV_OK;
+}
+
+int usv_volume_reset(usv_volume *vol, void *stream)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const usv::Layout L = usv::layout_for(v.g, v.mode);
+    cudaError_t e = usv::launch_zero(v.acc, L.val - L.acc, v.num_sms, st);
+    if (e == cudaSuccess)
+        e = usv::launch_zero(v.status, usv::kAlign, v.num_sms, st);
+    return usv::cuda_rc(e);
+}
+
+int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                      void *stream)
+{
+    if (!vol || !cal || n < 0)
+        return USV_ERR_ARG;
+    if (n == 0)
+        return USV_OK;
+    if (!images_dev || !poses_dev || (reinterpret_cast<uintptr_t>(poses_dev) & 7) != 0)
+        return USV_ERR_ARG;
+    if (H < 1 || W < 1)
+        return USV_ERR_ARG;
+    if (H > usv::kMaxDim || W > usv::kMaxDim)
+        return USV_ERR_RANGE;
+    if (dtype != USV_U8 && dtype != USV_F32)
+        return USV_ERR_ARG;
+    if (cal->geom != USV_LINEAR && cal->geom != USV_CONVEX)
+        return USV_ERR_ARG;
+    if (!usv::affine_ok(cal->image_to_probe))
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    usv::SetupParams sp;
+    std::memcpy(sp.K, cal->image_to_probe, sizeof(sp.K));
+    for (int a = 0; a < 3; ++a) {
+        sp.s[a] = v.spacing[a];
+        sp.o[a] = v.origin[a];
+    }
+    const bool convex = cal->geom == USV_CONVEX;
+    sp.convex = convex ? 1 : 0;
+    if (convex) {
+        if (!(std::isfinite(cal->r0_mm) && std::isfinite(cal->dr_mm) &&
+              std::isfinite(cal->sector_deg)))
+            return USV_ERR_ARG;
+        if (!(cal->r0_mm >= 0.0 && cal->dr_mm > 0.0 && cal->sector_deg > 0.0 &&
+              cal->sector_deg < 180.0) || W < 2)
+            return USV_ERR_ARG;
+        if (cal->r0_mm + (H - 1) * cal->dr_mm > 16384.0)
+            return USV_ERR_RANGE;
+        sp.sx = 1.0;
+        sp.sy = 1.0;
+    } else {
+        if (!(std::isfinite(cal->sx_mm) && std::isfinite(cal->sy_mm) && cal->sx_mm > 0.0 &&
+              cal->sy_mm > 0.0))
+            return USV_ERR_ARG;
+        sp.sx = cal->sx_mm;
+        sp.sy = cal->sy_mm;
+    }
+    if (v.mode == USV_PNN && (dtype != USV_U8 || convex))
+        return USV_ERR_UNSUPPORTED;
+
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t elt = dtype == USV_U8 ? 1 : 4;
+    const size_t frame_bytes = (size_t)H * W * elt;
+    cudaError_t e = cudaSuccess;
+    if (convex)
+        e = usv::launch_beam_setup(v.beams, W, cal->sector_deg, st);
+    for (int c0 = 0; c0 < n && e == cudaSuccess; c0 += usv::kRecCap) {
+        const int nc = n - c0 < usv::kRecCap ? n - c0 : usv::kRecCap;
+        e = usv::launch_frame_setup(poses_dev + (size_t)c0 * 16, nc, sp, v.rec, v.status, st);
+        if (e != cudaSuccess)
+            break;
+        const char *img = static_cast<const char *>(images_dev) + (size_t)c0 * frame_bytes;
+        if (v.mode == USV_PNN)
+            e = usv::launch_insert_pnn(v, reinterpret_cast<const uint8_t *>(img), nc, H, W, st);
+        else
+            e = usv::launch_insert_trilinear(v, img, dtype == USV_F32, nc, H, W, sp.convex,
+                                             cal->r0_mm, cal->dr_mm, st);
+    }
+    if (e == cudaErrorNotSupported)
+        return USV_ERR_UNSUPPORTED;
+    return usv::cuda_rc(e);
+}
+
+int usv_fill_holes(usv_volume *vol, int32_t radius, void *stream)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    if (radius != 1)
+        return USV_ERR_UNSUPPORTED;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return usv::cuda_rc(v.mode == USV_PNN ? usv::launch_fill_pnn(v, st)
+                                          : usv::launch_fill_trilinear(v, st));
+}
+
+int usv_project_depth_band(usv_volume *vol, int32_t z_lo, int32_t z_hi, float *out_dev,
+                           uint16_t *count_dev, void *stream)
+{
+    if (!vol || !out_dev)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    if (z_lo < 0 || z_hi > v.g.nz || z_lo >= z_hi)
+        return USV_ERR_RANGE;
+    if (z_hi - z_lo > 65535)
+        return USV_ERR_RANGE;
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    return usv::cuda_rc(v.mode == USV_PNN
+                            ? usv::launch_project_u8(v, z_lo, z_hi, out_dev, count_dev, st)
+                            : usv::launch_project_f32(v, z_lo, z_hi, out_dev, count_dev, st));
+}
+
+int usv_volume_read(usv_volume *vol, int32_t what, void *dst_dev, void *stream)
+{
+    if (!vol || !dst_dev)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)v.g.nx * v.g.ny * v.g.nz;
+    switch (what) {
+    case USV_READ_ACCUM:
+        return usv::cuda_rc(cudaMemcpyAsync(dst_dev, v.acc, n * 8, cudaMemcpyDeviceToDevice, st));
+    case USV_READ_VALUES:
+        return usv::cuda_rc(cudaMemcpyAsync(dst_dev, v.val, n * (v.mode == USV_PNN ? 1 : 4),
+                                            cudaMemcpyDeviceToDevice, st));
+    case USV_READ_MASK:
+        return usv::cuda_rc(usv::launch_unpack_mask(v, static_cast<uint8_t *>(dst_dev), st));
+    default:
+        return USV_ERR_ARG;
+    }
+}
+
+int usv_volume_write_accum(usv_volume *vol, const void *src_dev, void *stream)
+{
+    if (!vol || !src_dev)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    usv::DeviceGuard g(v.device);
+    const size_t n = (size_t)v.g.nx * v.g.ny * v.g.nz;
+    return usv::cuda_rc(cudaMemcpyAsync(v.acc, src_dev, n * 8, cudaMemcpyDeviceToDevice,
+                                        static_cast<cudaStream_t>(stream)));
+}
+
+int usv_status(usv_volume *vol, void *stream)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t bits = 0;
+    int rc = usv::cuda_rc(cudaStreamSynchronize(st));
+    if (rc == USV_OK)
+        rc = usv::cuda_rc(cudaMemcpy(&bits, v.status, sizeof(bits), cudaMemcpyDeviceToHost));
+    if (rc == USV_OK && bits != 0)
+        rc = usv::cuda_rc(cudaMemset(v.status, 0, sizeof(bits)));
+    if (rc != USV_OK)
+        return rc;
+    return (int)(bits & 0x7FFFFFFFu);
+}
+
+}  // extern "C"

@@ -1,0 +1,75 @@
+// Internal declarations shared by the usvol translation units (not part of
+// the public ABI, which is include/usvol.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/usvol.h"
+
+namespace usv {
+
+// Per-frame set-up record written by k_frame_setup (A0) into the volume's
+// scratch area and read by the insertion kernels.
+struct FrameRec {
+    long long q[9];  // Q31.32 per-step map: A (per column), B (per row), C (pixel 0,0)
+    double d[9];     // FP64 map; linear: same as q unquantised; convex: per-mm factors
+    int valid;       // 0: frame skipped (bad pose)
+    int pad[3];
+};
+static_assert(sizeof(FrameRec) == 160, "FrameRec layout");
+
+// Host-side handle behind usv_volume*.
+struct Volume {
+    usv_grid g;
+    double spacing[3];
+    double origin[3];
+    int mode;
+    char *base;
+    size_t bytes;
+    void *acc;          // PNN: unsigned long long[N]; trilinear: float2[N] (S, W)
+    void *val;          // PNN: uint8_t[N]; trilinear: float[N]
+    uint32_t *mask;     // [nz][ny][nxw] bit words, bit x%32 of word x/32
+    int nxw;
+    FrameRec *rec;      // scratch: kRecCap records
+    double2 *beams;     // scratch: kBeamCap (sin, cos) pairs for convex beams
+    uint32_t *status;   // one word of USV_STATUS_* bits
+    int num_sms;
+    int device;
+};
+
+constexpr int kRecCap = 4096;      // frames per set-up + insert launch pair
+constexpr int kBeamCap = 32768;    // max W
+constexpr int kMaxDim = 32768;     // max H, W
+
+struct Layout {
+    size_t acc, val, mask, rec, beams, status, total;
+};
+Layout layout_for(usv_grid g, int mode);
+
+// Set-up parameters passed by value to k_frame_setup.
+struct SetupParams {
+    double K[16];
+    double sx, sy;        // linear: mm per column / row; convex: 1, 1 (per mm)
+    double s[3], o[3];
+    int convex;
+};
+
+// ---- launchers (each in its own translation unit) ----
+cudaError_t launch_frame_setup(const double *poses, int n, const SetupParams &sp, FrameRec *rec,
+                               uint32_t *status, cudaStream_t st);
+cudaError_t launch_beam_setup(double2 *beams, int W, double sector_deg, cudaStream_t st);
+cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H, int W,
+                              cudaStream_t st);
+cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
+                                    int W, int convex, double r0, double dr, cudaStream_t st);
+cudaError_t launch_fill_pnn(const Volume &v, cudaStream_t st);
+cudaError_t launch_fill_trilinear(const Volume &v, cudaStream_t st);
+cudaError_t launch_project_u8(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
+                              cudaStream_t st);
+cudaError_t launch_project_f32(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
+                               cudaStream_t st);
+cudaError_t launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t st);
+cudaError_t launch_unpack_mask(const Volume &v, uint8_t *dst, cudaStream_t st);
+
+}  // namespace usv

@@ -1,0 +1,271 @@
+"""Thin ctypes binding to libusvol.so (include/usvol.h).
+
+Argument marshalling only: every step of the path runs in the library's
+CUDA kernels.  PyTorch supplies device memory (the volume storage, frames,
+poses, outputs) and the CUDA stream.  There is no CPU fallback: if the
+library is missing this module raises.
+
+The functions keep the C names without the ``usv_`` prefix
+(``volume_bytes``, ``volume_create``, ``insert_frames``, ``fill_holes``,
+``project_depth_band``, ``volume_read``, ``status``); ``Volume`` bundles
+them with torch-owned storage.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libusvol.so")
+
+OK, ERR_ARG, ERR_RANGE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+STATUS_BAD_POSE, STATUS_SATURATED, STATUS_TIMEOUT = 0x1, 0x2, 0x4
+PNN, TRILINEAR = 0, 1
+LINEAR, CONVEX = 0, 1
+U8, F32 = 0, 1
+READ_ACCUM, READ_VALUES, READ_MASK = 0, 1, 2
+
+# every symbol declared in include/usvol.h
+EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_volume_reset",
+           "usv_insert_frames", "usv_fill_holes", "usv_project_depth_band", "usv_volume_read",
+           "usv_volume_write_accum", "usv_status", "usv_strerror", "usv_last_cuda_error",
+           "usv_abi_version")
+
+
+class UsvError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = f"{what}: {strerror(code)} ({code})"
+        if code == ERR_CUDA:
+            msg += f": {lib().usv_last_cuda_error().decode()}"
+        super().__init__(msg)
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Calibration(ctypes.Structure):
+    _fields_ = [("image_to_probe", ctypes.c_double * 16), ("geom", ctypes.c_int32),
+                ("sx_mm", ctypes.c_double), ("sy_mm", ctypes.c_double),
+                ("r0_mm", ctypes.c_double), ("dr_mm", ctypes.c_double),
+                ("sector_deg", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libusvol.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, Z = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+            D3 = ctypes.POINTER(ctypes.c_double)
+            L.usv_volume_bytes.argtypes = [Grid, I]
+            L.usv_volume_bytes.restype = Z
+            L.usv_volume_create.argtypes = [Grid, D3, D3, I, P, Z, ctypes.POINTER(P)]
+            L.usv_volume_create.restype = ctypes.c_int
+            L.usv_volume_destroy.argtypes = [P]
+            L.usv_volume_destroy.restype = ctypes.c_int
+            L.usv_volume_reset.argtypes = [P, P]
+            L.usv_volume_reset.restype = ctypes.c_int
+            L.usv_insert_frames.argtypes = [P, P, I, I, I, I, P, ctypes.POINTER(Calibration), P]
+            L.usv_insert_frames.restype = ctypes.c_int
+            L.usv_fill_holes.argtypes = [P, I, P]
+            L.usv_fill_holes.restype = ctypes.c_int
+            L.usv_project_depth_band.argtypes = [P, I, I, P, P, P]
+            L.usv_project_depth_band.restype = ctypes.c_int
+            L.usv_volume_read.argtypes = [P, I, P, P]
+            L.usv_volume_read.restype = ctypes.c_int
+            L.usv_volume_write_accum.argtypes = [P, P, P]
+            L.usv_volume_write_accum.restype = ctypes.c_int
+            L.usv_status.argtypes = [P, P]
+            L.usv_status.restype = ctypes.c_int
+            L.usv_strerror.argtypes = [ctypes.c_int]
+            L.usv_strerror.restype = ctypes.c_char_p
+            L.usv_last_cuda_error.argtypes = []
+            L.usv_last_cuda_error.restype = ctypes.c_char_p
+            L.usv_abi_version.argtypes = []
+            L.usv_abi_version.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().usv_strerror(int(code)).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise UsvError(rc, what)
+    return rc
+
+
+def _d3(v) -> ctypes.Array:
+    return (ctypes.c_double * 3)(*[float(x) for x in v])
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def make_calibration(image_to_probe, geom="linear", sx=0.0, sy=0.0, r0=0.0, dr=0.0,
+                     sector_deg=0.0) -> Calibration:
+    m = np.ascontiguousarray(np.asarray(image_to_probe, dtype=np.float64).reshape(16))
+    return Calibration((ctypes.c_double * 16)(*m.tolist()), CONVEX if geom == "convex" else LINEAR,
+                       float(sx), float(sy), float(r0), float(dr), float(sector_deg))
+
+
+def _mode(mode) -> int:
+    return {"pnn": PNN, "trilinear": TRILINEAR}.get(mode, mode)
+
+
+# ---------------------------------------------------------------- C-named calls
+
+def volume_bytes(grid, mode) -> int:
+    return int(lib().usv_volume_bytes(Grid(*grid), _mode(mode)))
+
+
+def volume_create(grid, spacing, origin, mode, storage_ptr: int, storage_bytes: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().usv_volume_create(Grid(*grid), _d3(spacing), _d3(origin), _mode(mode),
+                                   ctypes.c_void_p(storage_ptr), storage_bytes, ctypes.byref(h)),
+           "usv_volume_create")
+    return h.value
+
+
+def volume_destroy(handle: int) -> None:
+    _check(lib().usv_volume_destroy(ctypes.c_void_p(handle)), "usv_volume_destroy")
+
+
+def volume_reset(handle: int, stream=None) -> None:
+    _check(lib().usv_volume_reset(ctypes.c_void_p(handle), ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_volume_reset")
+
+
+def insert_frames(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
+                  poses_ptr: int, cal: Calibration, stream=None) -> None:
+    _check(lib().usv_insert_frames(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H, W,
+                                   dtype, ctypes.c_void_p(poses_ptr), ctypes.byref(cal),
+                                   ctypes.c_void_p(_stream_ptr(stream))), "usv_insert_frames")
+
+
+def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
+    _check(lib().usv_fill_holes(ctypes.c_void_p(handle), radius,
+                                ctypes.c_void_p(_stream_ptr(stream))), "usv_fill_holes")
+
+
+def project_depth_band(handle: int, z_lo: int, z_hi: int, out_ptr: int, count_ptr: int | None,
+                       stream=None) -> None:
+    _check(lib().usv_project_depth_band(ctypes.c_void_p(handle), z_lo, z_hi,
+                                        ctypes.c_void_p(out_ptr), ctypes.c_void_p(count_ptr or 0),
+                                        ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_project_depth_band")
+
+
+def volume_read(handle: int, what: int, dst_ptr: int, stream=None) -> None:
+    _check(lib().usv_volume_read(ctypes.c_void_p(handle), what, ctypes.c_void_p(dst_ptr),
+                                 ctypes.c_void_p(_stream_ptr(stream))), "usv_volume_read")
+
+
+def volume_write_accum(handle: int, src_ptr: int, stream=None) -> None:
+    _check(lib().usv_volume_write_accum(ctypes.c_void_p(handle), ctypes.c_void_p(src_ptr),
+                                        ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_volume_write_accum")
+
+
+def status(handle: int, stream=None) -> int:
+    return _check(lib().usv_status(ctypes.c_void_p(handle), ctypes.c_void_p(_stream_ptr(stream))),
+                  "usv_status")
+
+
+# ---------------------------------------------------------------- convenience
+
+class Volume:
+    """A reconstruction volume in torch-owned device storage."""
+
+    def __init__(self, grid, spacing, origin=(0.0, 0.0, 0.0), mode="pnn", device="cuda"):
+        self.grid = tuple(int(g) for g in grid)
+        self.mode = _mode(mode)
+        self.spacing = tuple(float(s) for s in spacing)
+        self.origin = tuple(float(o) for o in origin)
+        nbytes = volume_bytes(self.grid, self.mode)
+        if nbytes == 0:
+            raise UsvError(ERR_ARG, f"invalid grid {self.grid}")
+        self.storage = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.handle = volume_create(self.grid, self.spacing, self.origin, self.mode,
+                                    self.storage.data_ptr(), nbytes)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                volume_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    @property
+    def shape(self):
+        nx, ny, nz = self.grid
+        return (nz, ny, nx)
+
+    def reset(self, stream=None):
+        volume_reset(self.handle, stream)
+
+    def insert(self, images: torch.Tensor, poses: torch.Tensor, cal: Calibration, stream=None):
+        assert images.is_cuda and poses.is_cuda and images.is_contiguous() and poses.is_contiguous()
+        assert poses.dtype == torch.float64
+        n, H, W = images.shape
+        dt = U8 if images.dtype == torch.uint8 else F32
+        if dt == F32:
+            assert images.dtype == torch.float32
+        insert_frames(self.handle, images.data_ptr(), n, H, W, dt, poses.data_ptr(), cal, stream)
+
+    def fill(self, stream=None):
+        fill_holes(self.handle, 1, stream)
+
+    def project(self, z_lo, z_hi, out=None, count=None, stream=None):
+        nz, ny, nx = self.shape
+        dev = self.storage.device
+        if out is None:
+            out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+        if count is None:
+            count = torch.empty((ny, nx), dtype=torch.int16, device=dev)
+        project_depth_band(self.handle, z_lo, z_hi, out.data_ptr(),
+                           count.data_ptr() if count is not False else None, stream)
+        return out, count
+
+    def read(self, what, stream=None) -> torch.Tensor:
+        dev = self.storage.device
+        if what == READ_ACCUM:
+            dst = torch.empty(self.shape + ((2,) if self.mode == TRILINEAR else ()),
+                              dtype=torch.float32 if self.mode == TRILINEAR else torch.int64,
+                              device=dev)
+        elif what == READ_VALUES:
+            dst = torch.empty(self.shape, dtype=torch.uint8 if self.mode == PNN else torch.float32,
+                              device=dev)
+        else:
+            dst = torch.empty(self.shape, dtype=torch.uint8, device=dev)
+        volume_read(self.handle, what, dst.data_ptr(), stream)
+        return dst
+
+    def status(self, stream=None) -> int:
+        return status(self.handle, stream)
+
+
+def calibration_of(w) -> Calibration:
+    """Calibration struct for a synth.Workload (or any object with the same fields)."""
+    return make_calibration(w.calib, w.geom, w.sx, w.sy, w.r0, w.dr, w.sector_deg)

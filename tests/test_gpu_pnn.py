@@ -1,0 +1,199 @@
+"""GPU parity of the nearest-neighbour path (insert, fill, project) against the
+CPU oracle, through the C ABI.  Bit-exact: the path is integer end to end
+except the final FP32 division of the projection, which both sides take as
+one correctly rounded division of exact values."""
+import numpy as np
+import pytest
+
+from helpers import assert_pnn_bit_exact, build_library, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    build_library()
+
+
+def test_tiny_pnn_config_bit_exact():
+    from paper_2412_00058_gb300 import synth
+    w = synth.tiny_pnn()
+    g, o = gpu_run(w), oracle_run(w)
+    assert g["status"] == 0 and o["skipped"] == 0
+    assert_pnn_bit_exact(g, o)
+    assert o["cnt"].sum() > 500_000
+
+
+def test_whole_spine_piece_bit_exact_many_tiles_ragged_tail():
+    """480x640 frames: 128-column tiles leave a 96-column tail, 64-row tiles;
+    48 frames span several frame groups with a ragged last group."""
+    from paper_2412_00058_gb300 import synth
+    w = synth.whole_spine(n=47, grid=(270, 90, 200), y_start_mm=3.0, y_span_mm=20.0)
+    g, o = gpu_run(w), oracle_run(w)
+    assert g["status"] == 0
+    assert_pnn_bit_exact(g, o)
+
+
+@pytest.mark.parametrize("H,W", [(37, 100), (64, 33), (5, 7)])
+def test_scalar_load_path_for_ragged_widths(H, W):
+    from paper_2412_00058_gb300 import synth
+    w = synth.tiny_pnn(seed=5, n=9, H=H, W=W, px=0.21, grid=(48, 40, 44), tilt_deg=15.0,
+                       sweep_mm=5.0, y0_mm=3.0, band=(3, 30))
+    assert_pnn_bit_exact(gpu_run(w), oracle_run(w))
+
+
+def test_misaligned_frame_pointer_takes_scalar_path():
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    w = synth.tiny_pnn(seed=6, n=5, H=32, W=32, px=0.25, grid=(40, 40, 40), sweep_mm=4.0,
+                       y0_mm=2.0, band=(0, 40))
+    buf = torch.empty(w.images.size + 1, dtype=torch.uint8, device="cuda")
+    buf[1:] = torch.from_numpy(w.images.reshape(-1)).cuda()
+    imgs = buf[1:].view(w.images.shape)
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+    vol.reset()
+    vol.insert(imgs, torch.from_numpy(w.poses).cuda(), usvol.calibration_of(w))
+    acc = vol.read(usvol.READ_ACCUM).cpu().numpy().view(np.uint64)
+    o = oracle_run(w)
+    assert np.array_equal(acc & np.uint64(0xFFFFFFFF), o["sum"])
+    assert np.array_equal(acc >> np.uint64(32), o["cnt"].astype(np.uint64))
+
+
+def test_incremental_inserts_equal_one_batch():
+    """The paper's incremental method: inserting frames in uneven batches on
+    top of the existing volume gives the same volume as one call."""
+    from paper_2412_00058_gb300 import synth
+    w = synth.whole_spine(n=30, grid=(270, 60, 200), y_start_mm=5.0, y_span_mm=10.0)
+    a = gpu_run(w, splits=[1, 7, 3, 19])
+    b = gpu_run(w)
+    for k in ("sum", "cnt", "val", "has", "proj"):
+        assert np.array_equal(a[k], b[k])
+    assert_pnn_bit_exact(a, oracle_run(w))
+
+
+def test_more_frames_than_one_setup_chunk():
+    from paper_2412_00058_gb300 import synth
+    w = synth.tiny_pnn(seed=7, n=4100, H=16, W=16, px=0.3, grid=(24, 64, 24), tilt_deg=5.0,
+                       sweep_mm=16.0, y0_mm=1.0, band=(2, 20))
+    assert_pnn_bit_exact(gpu_run(w), oracle_run(w))
+
+
+def test_frames_outside_volume_and_empty_batch():
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    w = synth.tiny_pnn(seed=8, n=4, H=32, W=32, grid=(32, 32, 32), band=(0, 32))
+    w.poses[:, 1, 3] += 500.0                     # far along y: nothing lands
+    g = gpu_run(w)
+    assert g["cnt"].sum() == 0 and g["has"].sum() == 0 and not g["proj"].any()
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+    vol.reset()
+    e = torch.empty((0, 32, 32), dtype=torch.uint8, device="cuda")
+    p = torch.empty((0, 4, 4), dtype=torch.float64, device="cuda")
+    vol.insert(e, p, usvol.calibration_of(w))
+    assert vol.status() == 0
+
+
+def test_bad_poses_are_skipped_and_reported():
+    from paper_2412_00058_gb300 import synth, usvol
+    w = synth.tiny_pnn(seed=9, n=12, H=48, W=48, grid=(64, 64, 64), band=(10, 40))
+    w.poses[3, 0, 3] = np.nan
+    w.poses[5, 3, 0] = 1e-3                       # not affine
+    w.poses[7, 2, 3] = 1e12                       # out of range
+    g, o = gpu_run(w), oracle_run(w)
+    assert o["skipped"] == 3
+    assert g["status"] & usvol.STATUS_BAD_POSE
+    assert_pnn_bit_exact(g, o)
+
+
+def test_steep_and_coarse_frames_use_direct_atomics():
+    """Pixels larger than voxels and 60-degree tilts make tile boxes exceed
+    shared memory: those tiles send runs straight to HBM atomics."""
+    from paper_2412_00058_gb300 import synth
+    w = synth.tiny_pnn(seed=10, n=6, H=128, W=128, px=0.9, grid=(100, 100, 100),
+                       tilt_deg=60.0, sweep_mm=10.0, y0_mm=12.0, band=(20, 60))
+    assert_pnn_bit_exact(gpu_run(w), oracle_run(w))
+
+
+def test_fill_and_projection_on_hand_built_accumulators():
+    """Sparse random accumulators (holes everywhere, grid borders, nx not a
+    multiple of 32, ny not of 8) written through usv_volume_write_accum."""
+    import torch
+    import oracle
+    from paper_2412_00058_gb300 import usvol
+    rng = np.random.default_rng(12)
+    for grid in [(45, 13, 7), (32, 8, 1), (1, 1, 5), (70, 3, 40)]:
+        nx, ny, nz = grid
+        c = np.where(rng.random((nz, ny, nx)) < 0.3, rng.integers(1, 50, (nz, ny, nx)), 0)
+        s = (c * rng.integers(0, 256, (nz, ny, nx))).astype(np.uint64)
+        c = c.astype(np.uint32)
+        packed = (c.astype(np.uint64) << np.uint64(32)) | s
+        vol = usvol.Volume(grid, (0.5, 0.5, 0.5), (0, 0, 0), "pnn")
+        src = torch.from_numpy(packed.view(np.int64)).cuda()
+        usvol.volume_write_accum(vol.handle, src.data_ptr())
+        vol.fill()
+        for lo, hi in [(0, nz), (nz - 1, nz), (0, 1)]:
+            out, cnt = vol.project(lo, hi)
+            ov, oh = oracle.fill_pnn(s, c)
+            op, oc = oracle.project_u8(ov, oh, lo, hi)
+            assert np.array_equal(out.cpu().numpy(), op)
+            assert np.array_equal(cnt.cpu().numpy().view(np.uint16), oc)
+        assert np.array_equal(vol.read(usvol.READ_VALUES).cpu().numpy(), ov)
+        assert np.array_equal(vol.read(usvol.READ_MASK).cpu().numpy(), oh)
+
+
+def test_argument_errors_with_a_live_volume():
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    w = synth.tiny_pnn(n=2, H=16, W=16)
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+    imgs = torch.from_numpy(w.images).cuda()
+    poses = torch.from_numpy(w.poses).cuda()
+    L = usvol.lib()
+    cal = usvol.calibration_of(w)
+    sp = usvol._stream_ptr(None)
+
+    def ins(im=imgs.data_ptr(), n=2, H=16, W=16, dt=0, ps=poses.data_ptr(), c=cal):
+        import ctypes
+        return L.usv_insert_frames(vol.handle, im, n, H, W, dt, ps, ctypes.byref(c), sp)
+
+    assert ins(n=-1) == usvol.ERR_ARG
+    assert ins(H=0) == usvol.ERR_ARG
+    assert ins(W=40000) == usvol.ERR_RANGE
+    assert ins(dt=1) == usvol.ERR_UNSUPPORTED           # PNN takes uint8 frames
+    assert ins(ps=poses.data_ptr() + 4) == usvol.ERR_ARG
+    bad = usvol.calibration_of(w)
+    bad.image_to_probe[12] = 1.0
+    assert ins(c=bad) == usvol.ERR_ARG
+    bad = usvol.calibration_of(w)
+    bad.sx_mm = 0.0
+    assert ins(c=bad) == usvol.ERR_ARG
+    convex = usvol.make_calibration(np.eye(4), "convex", r0=40, dr=0.2, sector_deg=60)
+    assert ins(c=convex) == usvol.ERR_UNSUPPORTED       # PNN is linear-probe only
+    out = torch.empty((128, 128), dtype=torch.float32, device="cuda")
+    assert L.usv_project_depth_band(vol.handle, 5, 5, out.data_ptr(), None, sp) == usvol.ERR_RANGE
+    assert L.usv_project_depth_band(vol.handle, 0, 129, out.data_ptr(), None, sp) == usvol.ERR_RANGE
+    assert L.usv_fill_holes(vol.handle, 2, sp) == usvol.ERR_UNSUPPORTED
+    assert vol.status() == 0
+
+
+def test_deterministic_across_runs():
+    from paper_2412_00058_gb300 import synth
+    w = synth.whole_spine(n=20, grid=(270, 50, 200), y_start_mm=8.0, y_span_mm=8.0)
+    a, b = gpu_run(w), gpu_run(w)
+    for k in ("sum", "cnt", "val", "has", "proj", "pcnt"):
+        assert np.array_equal(a[k], b[k])
+
+
+@pytest.mark.slow
+def test_whole_spine_full_size_bit_exact():
+    """The full whole-spine sweep (3600 frames of 480x640 into 270x1840x200),
+    in the single launch the benchmark times, against the full oracle."""
+    from paper_2412_00058_gb300 import synth
+    w = synth.whole_spine()
+    g = gpu_run(w)
+    o = oracle_run(w)
+    assert g["status"] == 0 and o["skipped"] == 0
+    assert_pnn_bit_exact(g, o)
