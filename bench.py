@@ -1,0 +1,446 @@
+#!/usr/bin/env python
+"""Whole-spine sweep benchmark for the GB300 free-hand ultrasound path.
+
+One step = one pass of the whole path over one synthetic whole-spine sweep
+(3600 frames of 480x640 uint8 = 2 min at 30 fps, 550 mm along the spine):
+reset the 270x1840x200 volume, insert all frames (pixel nearest neighbour),
+normalise + 3x3x3 hole fill, project the 35-45 mm depth band.  Inputs are
+resident in HBM when the timed region starts (they are larger than L2, so no
+flush is needed between steps).
+
+Prints one JSON line (rank 0):
+  value      frames/s of the whole job (all ranks), CUDA-event timed
+  e2e        the same metric through the public API from pinned HOST buffers,
+             frames streamed host->device in 300-frame batches overlapped
+             with insertion, projection read back every step
+  roofline   the dominant kernel (insertion): algorithmic bytes / its event-
+             timed launch duration vs the measured HBM copy bandwidth
+  cpu_baseline  the CPU oracle on a bounded sample of the same sweep
+  clocks     nvidia-smi SM clocks / throttle reasons sampled while timing
+
+--impl reference times the CPU oracle (the only reference: the paper
+publishes no code) on the same metric.  Multi-GPU: replicas only -- every
+rank reconstructs its own sweep with no collective in the data path; the
+barrier and a MAX all-reduce of the elapsed time bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("frames/s & voxel-updates/s (full-spine sweep) vs HBM roofline; "
+          "p99 frame-to-render ms")
+WORKLOAD = ("whole-spine linear-probe sweep: 3600 frames 480x640 uint8, 550 mm along y, "
+            "+-20 mm sway, +-10 deg tilt; volume 270x1840x200 @ 0.3 mm; PNN insert + 3x3x3 "
+            "fill + depth band [117,150)")
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="usvol", choices=["usvol", "reference"])
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--frames", type=int, default=3600,
+                   help="frames of the sweep (fewer = a shorter piece at the same frame "
+                        "spacing; for profiling captures)")
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------- distributed
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def init_dist(backend: str):
+    import torch.distributed as dist
+    rank, local, world = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return rank, local, world
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """MAX all-reduce of a scalar (no-op on one process)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(device=None):
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        if device is not None and device.type == "cuda":
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 100 ms, timestamped."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append((time.perf_counter(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float):
+        if not self.samples:
+            return None
+        inside = [p for t, p in self.samples if t0 <= t <= t1]
+        if not inside:  # timed region shorter than one sample period: nearest sample
+            mid = 0.5 * (t0 + t1)
+            inside = [min(self.samples, key=lambda s: abs(s[0] - mid))[1]]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in inside if num(p[1]) is not None]
+        mx = [num(p[2]) for p in inside if num(p[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for p in inside for i in range(4)
+                          if p[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inside)}
+
+
+# ---------------------------------------------------------------- peaks
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- workload
+
+def sweep_workload(frames: int = 3600):
+    from paper_2412_00058_gb300 import synth
+    if frames >= 3600:
+        return synth.whole_spine()
+    return synth.whole_spine(n=frames, y_span_mm=550.0 * (frames - 1) / 3599.0)
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_sweep_seconds(w, frac: float, rng_offset: int = 0, acc=None):
+    """Time the oracle on a bounded sample of the sweep and scale it to the
+    whole sweep: insert `frac` of the frames (from rng_offset) into the full
+    volume, then fill + project the y-slab those frames cover; the insert
+    time is scaled by 1/frac, the fill/project time by ny/slab.  The
+    accumulators are allocated and zeroed outside the timed calls (acc).
+    Returns (seconds per full sweep, description, CPU seconds spent)."""
+    import numpy as np
+    import oracle
+    n = w.n
+    k = max(1, int(round(n * frac)))
+    f0 = min(n - k, rng_offset)
+    nx, ny, nz = w.grid
+    if acc is None:
+        acc = (np.zeros((nz, ny, nx), np.uint64), np.zeros((nz, ny, nx), np.uint32))
+    s, c = acc
+    s.fill(0)
+    c.fill(0)
+    t0 = time.perf_counter()
+    oracle.insert_pnn(w.grid, w.images[f0:f0 + k], w.poses[f0:f0 + k], w.calib, w.sx, w.sy,
+                      w.spacing, w.origin, sum_=s, cnt=c)
+    t_ins = time.perf_counter() - t0
+    rows = max(3, int(round(ny * frac)))
+    y0 = int(np.clip(np.median(w.poses[f0:f0 + k, 1, 3]) / w.spacing[1] - rows / 2, 0, ny - rows))
+    ss = np.ascontiguousarray(s[:, y0:y0 + rows, :])
+    cc = np.ascontiguousarray(c[:, y0:y0 + rows, :])
+    t0 = time.perf_counter()
+    val, has = oracle.fill_pnn(ss, cc)
+    oracle.project_u8(val, has, *w.band)
+    t_fp = time.perf_counter() - t0
+    sweep = t_ins * (n / k) + t_fp * (ny / rows)
+    desc = (f"oracle insert of frames [{f0},{f0 + k}) of {n} (x{n / k:.1f}) + fill/project of "
+            f"y-slab [{y0},{y0 + rows}) of {ny} (x{ny / rows:.1f}); single thread")
+    return sweep, desc, t_ins + t_fp
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    from paper_2412_00058_gb300 import synth
+    import oracle
+    oracle.build()
+    import numpy as np
+    w = synth.whole_spine()
+    nx, ny, nz = w.grid
+    acc = (np.zeros((nz, ny, nx), np.uint64), np.zeros((nz, ny, nx), np.uint32))
+    frac = 12.0 / w.n                       # ~0.1 s of oracle work per step
+    for i in range(args.warmup):
+        oracle_sweep_seconds(w, frac, rng_offset=(i * 97) % w.n, acc=acc)
+    sweeps, cpu_s = [], 0.0
+    for i in range(args.steps):
+        s, desc, t = oracle_sweep_seconds(w, frac, rng_offset=(i * 389 + 1234) % w.n, acc=acc)
+        sweeps.append(s)
+        cpu_s += t
+    sweep = statistics.mean(sweeps)
+    value = w.n / sweep
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sweep * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                         "sample": f"per step: {desc}; {cpu_s:.1f} s of CPU work in total"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, local, world = init_dist("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    from paper_2412_00058_gb300 import build, synth, usvol
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(dev)
+    usvol.lib()
+
+    w = sweep_workload(args.frames)
+    nx, ny, nz = w.grid
+    lo, hi = w.band
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "pnn", device=dev)
+    imgs = torch.from_numpy(w.images).to(dev)
+    poses = torch.from_numpy(w.poses).to(dev)
+    cal = usvol.calibration_of(w)
+    out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    cnt = torch.empty((ny, nx), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    launches_per_step = 6  # reset: 2 clears; insert: set-up + insert; fill; project
+
+    def step(ev=None):
+        vol.reset(stream)
+        if ev is not None:
+            ev[0].record(stream)
+        vol.insert(imgs, poses, cal, stream)
+        if ev is not None:
+            ev[1].record(stream)
+        vol.fill(stream)
+        if ev is not None:
+            ev[2].record(stream)
+        vol.project(lo, hi, out=out, count=cnt, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    st = vol.status(stream)
+    if st != 0:
+        raise RuntimeError(f"device status {st:#x} after warm-up")
+    # distinct voxels touched by one sweep (one insert launch) and pixel hits
+    acc = vol.read(usvol.READ_ACCUM, stream)
+    counts = (acc >> 32)
+    touched = int((counts > 0).sum().item())
+    hits = int(counts.sum().item())
+    del acc, counts
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_stop = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev.index).start() if rank == 0 else None
+    time.sleep(0.25 if sampler else 0.0)
+    barrier(dev)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    e_start.record(stream)
+    for k in range(K):
+        step(evs[k])
+    e_stop.record(stream)
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    barrier(dev)
+    if sampler:
+        sampler.stop()
+    local_ms = e_start.elapsed_time(e_stop)
+    total_ms = max_over_ranks(local_ms, dev)
+    ms_per_step = total_ms / K
+    ins_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    fill_ms = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    proj_ms = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    frames = w.n * world * K
+    value = frames / (total_ms / 1e3)
+    vupd = hits * world * K / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (insertion)
+    peak, peak_kind = measured_peaks()
+    nvox = nx * ny * nz
+    frame_bytes = w.images.nbytes
+    ins_bytes = frame_bytes + 16 * touched
+    achieved = ins_bytes / (ins_ms / 1e3) / 1e9
+    fill_bytes = nvox * (8 + 1) + nz * ny * ((nx + 31) // 32) * 4
+    proj_bytes = (hi - lo) * ny * (nx + ((nx + 31) // 32) * 4 / 1) + ny * nx * 6
+    reset_bytes = nvox * 8
+    step_bytes = reset_bytes + ins_bytes + fill_bytes + proj_bytes
+
+    # ---- end to end through the public API from pinned host memory
+    e2e = None
+    if args.e2e_steps > 0:
+        h_imgs = torch.from_numpy(w.images).pin_memory()
+        h_poses = torch.from_numpy(w.poses).pin_memory()
+        h_out = torch.empty((ny, nx), dtype=torch.float32).pin_memory()
+        h_cnt = torch.empty((ny, nx), dtype=torch.int16).pin_memory()
+        d_imgs = torch.empty_like(imgs)
+        d_poses = torch.empty_like(poses)
+        copy_stream = torch.cuda.Stream(dev)
+        batch = 300
+        bounds = [(b, min(w.n, b + batch)) for b in range(0, w.n, batch)]
+
+        def e2e_step():
+            vol.reset(stream)
+            done = []
+            for b0, b1 in bounds:
+                with torch.cuda.stream(copy_stream):
+                    d_imgs[b0:b1].copy_(h_imgs[b0:b1], non_blocking=True)
+                    d_poses[b0:b1].copy_(h_poses[b0:b1], non_blocking=True)
+                    e = torch.cuda.Event()
+                    e.record(copy_stream)
+                done.append(e)
+            for (b0, b1), e in zip(bounds, done):
+                stream.wait_event(e)
+                vol.insert(d_imgs[b0:b1], d_poses[b0:b1], cal, stream)
+            vol.fill(stream)
+            vol.project(lo, hi, out=out, count=cnt, stream=stream)
+            h_out.copy_(out, non_blocking=True)
+            h_cnt.copy_(cnt, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        barrier(dev)
+        t_e0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        t_e = max_over_ranks(time.perf_counter() - t_e0, dev)
+        assert np.array_equal(h_out.numpy(), out.cpu().numpy())
+        e2e = {"value": w.n * world * args.e2e_steps / t_e, "unit": "frames/s",
+               "h2d_bytes_per_step": int(w.images.nbytes + w.poses.nbytes),
+               "d2h_bytes_per_step": int(h_out.numel() * 4 + h_cnt.numel() * 2),
+               "ms_per_step": t_e / args.e2e_steps * 1e3,
+               "pipeline": f"{len(bounds)} batches of {batch} frames, H2D on a copy stream "
+                           "overlapped with insertion"}
+
+    # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sweep_s, desc, cpu_work = oracle_sweep_seconds(w, 0.25)
+        cpu = {"value": w.n / sweep_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
+               "sample": f"{desc}; {cpu_work:.1f} s of CPU work"}
+
+    clocks = sampler.summary(t0, t1) if sampler else None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": K, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (1.1 GB frames, 795 MB accumulators)"},
+            "voxel_updates_per_s": vupd,
+            "stage_ms": {"insert": ins_ms, "fill": fill_ms, "project": proj_ms,
+                         "reset_and_gaps": ms_per_step - ins_ms - fill_ms - proj_ms},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "insert (PNN)",
+                         "algorithmic_bytes": ins_bytes, "peak_kind": peak_kind},
+            "pipeline_roofline": {"algorithmic_bytes_per_step": step_bytes,
+                                  "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
+                                  "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak},
+            "touched_voxels": touched, "pixel_hits": hits,
+            "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches_per_step * K,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    import torch.distributed as dist
+    if dist.is_initialized():
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -8,9 +8,9 @@
 // PNN means round half up in exact integer arithmetic; the weighted variant
 // divides in IEEE FP32.
 //
-// GB300 design: HBM-bound stencil.  A CTA owns a 32 x 8 (x, y) column tile
-// and marches along z through a slab of planes, keeping three halo'd planes
-// of accumulators in a shared-memory ring, so every accumulator is read from
+// GB300 design: HBM-bound stencil.  A CTA owns an (x, y) column tile and
+// marches along z through a slab of planes, keeping halo'd planes of
+// accumulators in a shared-memory ring, so every accumulator is read from
 // HBM once (plus a thin halo that neighbouring CTAs share through L2).  The
 // has-data mask is one warp ballot per 32 voxels of a row.
 #include "usv_internal.cuh"
@@ -60,56 +60,191 @@ __device__ __forceinline__ void load_plane(T (*pl)[PX], const T *acc, int z, con
     }
 }
 
-__global__ void __launch_bounds__(TX *TY) k_fill_pnn(FillArgs a)
+// ---- nearest-neighbour fill ------------------------------------------------
+//
+// CTA: 32 x 8 threads own a 32 x 16 (x, y) column tile (two rows per thread)
+// and march z.  Planes of packed accumulators (tile + 1-voxel halo) stream
+// into a 6-slot shared ring with cp.async, two planes ahead of use.  The
+// pooled 26-neighbour sums are separable: per plane, row sums over x
+// (shared), then 3x3 plane sums over y (registers, kept for three planes);
+// the 3x3x3 sum is the sum of three plane sums, own voxel included (an empty
+// voxel adds zero).  While every accumulator of the three planes is below
+// 2^26 (sum and count) the sums are exact in 32 bits; otherwise that plane
+// takes a direct 64-bit path.  Tiles whose three planes are all empty write
+// zeros without arithmetic.
+constexpr int FTX = 32, FTY = 16, FBY = 8;
+constexpr int FPX = FTX + 2, FPY = FTY + 2, FPLANE = FPX * FPY;
+constexpr int FSLOTS = 6;
+constexpr unsigned kBig = 1u << 26;
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
 {
-    __shared__ unsigned long long pl[3][PY][PX];
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 8 : 0;  // 0: zero-fill, nothing read
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// floor(S/C + 1/2) clamped to 255 for C > 0, S < 2^31, C < 2^31: an FP32
+// estimate of S/C is within one of floor(S/C); one exact integer correction
+// in each direction, then round half up from the exact remainder.
+__device__ __forceinline__ unsigned mean_round_small(unsigned S, unsigned C)
+{
+    const float qf = __fdividef(__uint2float_rn(S), __uint2float_rn(C));
+    if (qf >= 254.5f)
+        return (unsigned long long)S >= 255ull * C ? 255u : mean_round_u8(S, C);
+    unsigned q = (unsigned)qf;
+    unsigned long long qc = (unsigned long long)q * C;
+    if (qc > S) {
+        --q;
+        qc -= C;
+    } else if (qc + C <= S) {
+        ++q;
+        qc += C;
+    }
+    const unsigned r = S - (unsigned)qc;
+    q += (2u * r >= C) ? 1u : 0u;
+    return q > 255u ? 255u : q;
+}
+
+__global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
+{
+    __shared__ __align__(16) unsigned long long P[FSLOTS][FPY][FPX];
+    __shared__ uint2 R[FPY][FTX];
     const auto *acc = static_cast<const unsigned long long *>(a.acc);
     auto *val = static_cast<uint8_t *>(a.val);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
-    const int x = x0 + tx, y = y0 + ty;
-    const bool inside = x < a.nx && y < a.ny;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    const int x = x0 + tx;
     bool saturated = false;
 
-    load_plane(pl[(z0 + 2) % 3], acc, z0 - 1, a, x0, y0, tid);
-    load_plane(pl[z0 % 3], acc, z0, a, x0, y0, tid);
-    for (int z = z0; z < z1; ++z) {
-        load_plane(pl[(z + 1) % 3], acc, z + 1, a, x0, y0, tid);
-        __syncthreads();
-        const unsigned long long c0 = pl[z % 3][ty + 1][tx + 1];
-        unsigned v = 0;
-        bool has;
-        if ((c0 >> 32) != 0) {
-            saturated |= (c0 >> 32) >= (1u << 24);
-            v = mean_round_u8(c0 & 0xFFFFFFFFull, c0 >> 32);
-            has = true;
-        } else {
-            unsigned long long S = 0, C = 0;
-#pragma unroll
-            for (int dz = 0; dz < 3; ++dz) {
-                const int slot = (z + 2 + dz) % 3;  // planes z-1, z, z+1
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-                        const unsigned long long w = pl[slot][ty + dy][tx + dx];
-                        S += w & 0xFFFFFFFFull;
-                        C += w >> 32;
-                    }
+    auto issue = [&](int pl) {
+        if (pl <= z1) {
+            unsigned long long *dst = &P[(pl + FSLOTS) % FSLOTS][0][0];
+            for (int i = tid; i < FPLANE; i += FTX * FBY) {
+                const int ly = i / FPX, lx = i - ly * FPX;
+                const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
+                const bool ok = pl >= 0 && pl < a.nz && X >= 0 && X < a.nx && Y >= 0 && Y < a.ny;
+                cp_async8(dst + i, ok ? acc + ((size_t)pl * a.ny + Y) * a.nx + X : acc, ok);
             }
-            has = C != 0;
-            if (has)
-                v = mean_round_u8(S, C);
         }
-        const size_t i = ((size_t)z * a.ny + y) * a.nx + x;
-        if (inside)
-            val[i] = (uint8_t)v;
-        const unsigned bits = __ballot_sync(0xFFFFFFFFu, inside && has);
-        if (tx == 0 && y < a.ny)
-            a.mask[((size_t)z * a.ny + y) * a.nxw + blockIdx.x] = bits;
-        __syncthreads();
+        cp_async_commit();
+    };
+
+    uint2 B[3][2];       // 3x3 plane sums (S, C) of planes z-1, z, z+1 for rows ty, ty+8
+    int nzf[3] = {0, 0, 0}, bigf[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        B[k][0] = B[k][1] = make_uint2(0, 0);
+
+    issue(z0 - 1);
+    issue(z0);
+    for (int pl = z0 - 1; pl <= z1; ++pl) {
+        issue(pl + 2);
+        cp_async_wait<2>();
+        const int slot = (pl + FSLOTS) % FSLOTS;
+        const unsigned long long(*Pp)[FPX] = P[slot];
+        bool nzp = false, bigp = false;
+        for (int i = tid; i < FPLANE; i += FTX * FBY) {
+            const unsigned long long w = (&Pp[0][0])[i];
+            nzp |= w != 0ull;
+            bigp |= (unsigned)w >= kBig || (unsigned)(w >> 32) >= kBig;
+        }
+        const int nz_pl = __syncthreads_or(nzp);
+        const int big_pl = nz_pl ? __syncthreads_or(bigp) : 0;
+        uint2 Bn[2] = {make_uint2(0, 0), make_uint2(0, 0)};
+        if (nz_pl && !big_pl) {
+            for (int i = tid; i < FPY * FTX; i += FTX * FBY) {
+                const int ry = i / FTX, rx = i - ry * FTX;
+                const unsigned long long p0 = Pp[ry][rx], p1 = Pp[ry][rx + 1], p2 = Pp[ry][rx + 2];
+                R[ry][rx] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
+                                       (unsigned)(p0 >> 32) + (unsigned)(p1 >> 32) +
+                                           (unsigned)(p2 >> 32));
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int ly = ty + r * FBY;
+                const uint2 a0 = R[ly][tx], a1 = R[ly + 1][tx], a2 = R[ly + 2][tx];
+                Bn[r] = make_uint2(a0.x + a1.x + a2.x, a0.y + a1.y + a2.y);
+            }
+        }
+        // rotate: B[0] <- z-1, B[1] <- z, B[2] <- z+1 for output z = pl - 1
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            B[0][r] = B[1][r];
+            B[1][r] = B[2][r];
+            B[2][r] = Bn[r];
+        }
+        nzf[0] = nzf[1];
+        nzf[1] = nzf[2];
+        nzf[2] = nz_pl;
+        bigf[0] = bigf[1];
+        bigf[1] = bigf[2];
+        bigf[2] = big_pl;
+        const int z = pl - 1;
+        if (z < z0)
+            continue;
+        const int sz = (z + FSLOTS) % FSLOTS;
+        const bool any = nzf[0] | nzf[1] | nzf[2];
+        const bool big = bigf[0] | bigf[1] | bigf[2];
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const int ly = ty + r * FBY;
+            const int y = y0 + ly;
+            unsigned v = 0;
+            bool has = false;
+            if (any) {
+                const unsigned long long own = P[sz][ly + 1][tx + 1];
+                const unsigned c_own = (unsigned)(own >> 32);
+                if (!big) {
+                    if (c_own != 0u) {
+                        v = mean_round_small((unsigned)own, c_own);
+                        has = true;
+                    } else {
+                        // own count is 0; drop its sum too (only neighbours pool)
+                        const unsigned S = B[0][r].x + B[1][r].x + B[2][r].x - (unsigned)own;
+                        const unsigned C = B[0][r].y + B[1][r].y + B[2][r].y;
+                        has = C != 0u;
+                        if (has)
+                            v = mean_round_small(S, C);
+                    }
+                } else if (own >> 32) {
+                    saturated |= (own >> 32) >= (1ull << 24);
+                    v = mean_round_u8(own & 0xFFFFFFFFull, own >> 32);
+                    has = true;
+                } else {
+                    unsigned long long S = 0, C = 0;
+#pragma unroll
+                    for (int dz = 0; dz < 3; ++dz) {
+                        const int s2 = (z - 1 + dz + FSLOTS) % FSLOTS;
+#pragma unroll
+                        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                            for (int dx = 0; dx < 3; ++dx) {
+                                const unsigned long long w = P[s2][ly + dy][tx + dx];
+                                S += w & 0xFFFFFFFFull;
+                                C += w >> 32;
+                            }
+                    }
+                    has = C != 0;
+                    if (has)
+                        v = mean_round_u8(S, C);
+                }
+            }
+            const bool inside = x < a.nx && y < a.ny;
+            if (inside)
+                val[((size_t)z * a.ny + y) * a.nx + x] = (uint8_t)v;
+            const unsigned bits = __ballot_sync(0xFFFFFFFFu, inside && has);
+            if (tx == 0 && y < a.ny)
+                a.mask[((size_t)z * a.ny + y) * a.nxw + blockIdx.x] = bits;
+        }
     }
+    cp_async_wait<0>();
     if (__syncthreads_or(saturated) && tid == 0)
         atomicOr(a.status, USV_STATUS_SATURATED);
 }
@@ -183,8 +318,15 @@ dim3 fill_grid(const Volume &v, int *zchunk)
 cudaError_t launch_fill_pnn(const Volume &v, cudaStream_t st)
 {
     FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0};
-    const dim3 grid = fill_grid(v, &a.zchunk);
-    k_fill_pnn<<<grid, dim3(TX, TY), 0, st>>>(a);
+    const int gx = (v.g.nx + FTX - 1) / FTX, gy = (v.g.ny + FTY - 1) / FTY;
+    // ~6 waves of 6 resident CTAs per SM; slabs of at least 24 planes
+    const long long want = (long long)v.num_sms * 6 * 6;
+    long long zc = ((long long)gx * gy * v.g.nz + want - 1) / want;
+    zc = zc < 24 ? 24 : zc;
+    zc = zc > v.g.nz ? v.g.nz : zc;
+    a.zchunk = (int)zc;
+    const dim3 grid(gx, gy, (v.g.nz + a.zchunk - 1) / a.zchunk);
+    k_fill_pnn<<<grid, dim3(FTX, FBY), 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -10,8 +10,10 @@
 //    frames; each thread reads 16 pixels per 128-bit load (coalesced);
 //  * the tile's voxel bounding box over its frames is exact (the map is
 //    affine, so the extremes sit at the tile corners) -> the CTA accumulates
-//    into a dense shared-memory box with 64-bit shared atomics, then adds
-//    each touched box entry to HBM with one 64-bit global atomic;
+//    into a dense shared-memory box (separate 32-bit sum and count arrays:
+//    native shared atomics; a CTA sees at most 4*8192 pixels, so neither
+//    word can wrap), then adds each touched box entry to HBM with one
+//    packed 64-bit global atomic;
 //  * within a thread, consecutive pixels that hit the same voxel are merged
 //    in registers (about 3.6 pixels per voxel along a row for the
 //    whole-spine probe) before touching shared memory;
@@ -50,11 +52,23 @@ __device__ __forceinline__ unsigned long long pack(unsigned s, unsigned c)
     return ((unsigned long long)c << 32) | (unsigned long long)s;
 }
 
+// Target of a run: the CTA's shared box (sum and count words) or, in direct
+// mode, the packed HBM accumulators.
+struct Target {
+    unsigned *bsum;
+    unsigned *bcnt;
+    unsigned long long *acc;
+};
+
 template <bool SHARED>
-__device__ __forceinline__ void add_run(unsigned long long *target, unsigned key, unsigned s,
-                                        unsigned c)
+__device__ __forceinline__ void add_run(const Target &t, unsigned key, unsigned s, unsigned c)
 {
-    atomicAdd(target + key, pack(s, c));
+    if (SHARED) {
+        atomicAdd(t.bsum + key, s);
+        atomicAdd(t.bcnt + key, c);
+    } else {
+        atomicAdd(t.acc + key, pack(s, c));
+    }
 }
 
 // Walk one run of up to 16 pixels along a row.  q*: box-local Q31.32
@@ -64,9 +78,10 @@ template <bool VEC, bool CHECK, bool SHARED>
 __device__ __forceinline__ void walk_chunk(const uint32_t (&pw)[4], int npx, long long qx,
                                            long long qy, long long qz, long long ax, long long ay,
                                            long long az, unsigned ex, unsigned ey, unsigned ez,
-                                           unsigned long long *target)
+                                           const Target &t)
 {
-    unsigned cur = kNone, rs = 0, rc = 0;
+    unsigned cur = kNone, rs = 0;
+    int start = 0;
 #pragma unroll
     for (int p = 0; p < 16; ++p) {
         if (!VEC && p >= npx)
@@ -80,26 +95,25 @@ __device__ __forceinline__ void walk_chunk(const uint32_t (&pw)[4], int npx, lon
             key = ((unsigned)lz * ey + (unsigned)ly) * ex + (unsigned)lx;
         }
         if (key != cur) {
-            if (rc != 0 && cur != kOut)
-                add_run<SHARED>(target, cur, rs, rc);
+            if (p != 0 && cur != kOut)
+                add_run<SHARED>(t, cur, rs, (unsigned)(p - start));
             cur = key;
             rs = 0;
-            rc = 0;
+            start = p;
         }
         rs += (pw[p >> 2] >> (8 * (p & 3))) & 0xFFu;
-        rc += 1;
         qx += ax;
         qy += ay;
         qz += az;
     }
-    if (rc != 0 && cur != kOut)
-        add_run<SHARED>(target, cur, rs, rc);
+    if (cur != kOut)
+        add_run<SHARED>(t, cur, rs, (unsigned)((VEC ? 16 : npx) - start));
 }
 
 template <bool VEC, bool CHECK, bool SHARED>
 __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1, int v0, int v1,
                            const long long (&off)[3], unsigned ex, unsigned ey, unsigned ez,
-                           unsigned long long *target)
+                           const Target &target)
 {
     const int cpr = (u1 - u0 + 15) >> 4;  // chunks per row
     const int nchunks = cpr * (v1 - v0);
@@ -141,7 +155,7 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
 template <bool VEC>
 __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
 {
-    extern __shared__ unsigned long long box[];
+    extern __shared__ unsigned box[];  // [box_cap] sums, then [box_cap] counts
     __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
 
     const int tile = blockIdx.x;
@@ -199,16 +213,19 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
     if (mode == 1) {
         const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
         const unsigned bvol = ex * ey * ez;
-        for (unsigned i = threadIdx.x; i < bvol; i += kThreads)
-            box[i] = 0ull;
+        const Target t{box, box + a.box_cap, nullptr};
+        for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
+            t.bsum[i] = 0u;
+            t.bcnt[i] = 0u;
+        }
         __syncthreads();
         const long long off[3] = {(1LL << 31) - ((long long)s_lo[0] << 32),
                                   (1LL << 31) - ((long long)s_lo[1] << 32),
                                   (1LL << 31) - ((long long)s_lo[2] << 32)};
         if (s_check)
-            run_frames<VEC, true, true>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box);
+            run_frames<VEC, true, true>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, t);
         else
-            run_frames<VEC, false, true>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box);
+            run_frames<VEC, false, true>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, t);
         __syncthreads();
         // Flush: one warp per box row (fixed y, z), lanes along x.
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -216,18 +233,20 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
             const unsigned ly = row % ey, lz = row / ey;
             unsigned long long *dst =
                 a.acc + ((size_t)(lz + s_lo[2]) * a.ny + (ly + s_lo[1])) * a.nx + s_lo[0];
-            const unsigned long long *src = box + (size_t)row * ex;
+            const unsigned *src_s = t.bsum + (size_t)row * ex;
+            const unsigned *src_c = t.bcnt + (size_t)row * ex;
             for (unsigned lx = lane; lx < ex; lx += 32) {
-                const unsigned long long val = src[lx];
-                if (val != 0ull)
-                    atomicAdd(dst + lx, val);
+                const unsigned c = src_c[lx];
+                if (c != 0u)
+                    atomicAdd(dst + lx, pack(src_s[lx], c));
             }
         }
     } else {
         // Direct mode: keys are global linear indices into the whole grid.
         const long long off[3] = {1LL << 31, 1LL << 31, 1LL << 31};
+        const Target t{nullptr, nullptr, a.acc};
         run_frames<VEC, true, false>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
-                                     (unsigned)a.ny, (unsigned)a.nz, a.acc);
+                                     (unsigned)a.ny, (unsigned)a.nz, t);
     }
 }
 
@@ -255,7 +274,7 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.tiles_y = (H + a.th - 1) / a.th;
     a.fpc = 4;
     const int smem = 48 * 1024;
-    a.box_cap = smem / 8;
+    a.box_cap = smem / 8;  // entries: one 32-bit sum + one 32-bit count each
     const bool vec = (W % 16 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0);
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
