@@ -6,21 +6,25 @@
 // integer, so the result is exact and independent of execution order.
 //
 // GB300 design:
-//  * one CTA = a tile of TH rows x (16*TWC) columns of FPC consecutive
-//    frames; each thread reads 16 pixels per 128-bit load (coalesced);
+//  * one CTA = a tile of up to 128 columns x 64 rows of FPC consecutive
+//    frames; a warp covers one 128-pixel row segment, each lane four
+//    consecutive pixels read with one coalesced 32-bit load; warps take
+//    every 8th row;
 //  * the tile's voxel bounding box over its frames is exact (the map is
-//    affine, so the extremes sit at the tile corners) -> the CTA accumulates
-//    into a dense shared-memory box (separate 32-bit sum and count arrays:
-//    native shared atomics; a CTA sees at most 4*8192 pixels, so neither
-//    word can wrap), then adds each touched box entry to HBM with one
-//    packed 64-bit global atomic;
-//  * within a thread, consecutive pixels that hit the same voxel are merged
-//    in registers (about 3.6 pixels per voxel along a row for the
-//    whole-spine probe) before touching shared memory;
-//  * coordinates advance by exact 64-bit adds (two 32-bit ops per axis);
-//    bounds checks run only in tiles whose box was clipped by the grid;
-//  * tiles whose box does not fit in shared memory (pixels as coarse as
-//    voxels, or steep poses) send each run straight to HBM atomics.
+//    affine, so the extremes sit at the tile corners), so the CTA can
+//    accumulate into a dense shared-memory box and then add each touched
+//    entry to HBM with one packed 64-bit global atomic;
+//  * per pixel: three exact 64-bit coordinate adds, the box index, one
+//    native 32-bit shared atomic.  In one step all 32 lanes handle pixels 4
+//    columns apart, i.e. (nearly always) different voxels, so the atomics
+//    neither diverge nor collide;
+//  * box entry layout: if the frames' bound on pixels per voxel (set-up
+//    kernel) keeps every count of the CTA below 1024, one word holds
+//    count (10 bits) | sum (22 bits) -> one atomic per pixel; otherwise
+//    two words (sum, count) -> two atomics; if the box does not fit in
+//    shared memory (pixels as coarse as voxels, steep poses) every pixel
+//    goes straight to an HBM atomic;
+//  * bounds checks run only in tiles whose box was clipped by the grid.
 #include <climits>
 
 #include "usv_internal.cuh"
@@ -30,8 +34,13 @@ namespace usv {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr unsigned kOut = 0xFFFFFFFEu;   // run key of pixels outside the box
-constexpr unsigned kNone = 0xFFFFFFFFu;  // no run open
+constexpr int kWarps = kThreads / 32;
+constexpr int kTileW = 128;          // columns per tile (32 lanes x 4 pixels)
+constexpr int kSmem = 32 * 1024;     // dynamic shared memory per CTA
+constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
+constexpr int kPackedMaxCount = 1023;
+
+enum { MODE_SKIP = 0, MODE_PACKED = 1, MODE_SPLIT = 2, MODE_DIRECT = 3 };
 
 struct PnnArgs {
     const uint8_t *img;
@@ -39,115 +48,88 @@ struct PnnArgs {
     const FrameRec *rec;
     unsigned long long *acc;
     int nx, ny, nz;
-    int twc, th;            // tile: twc 16-pixel chunks wide, th rows high
-    int tiles_x, tiles_y;   // tiles per frame
+    int th;                 // rows per tile
+    int tiles_x;            // tiles per frame along u
     int fpc;                // frames per CTA
-    int box_cap;            // shared box capacity (entries)
 };
 
 __device__ __forceinline__ int hi32(long long q) { return (int)(q >> 32); }
 
-__device__ __forceinline__ unsigned long long pack(unsigned s, unsigned c)
+__device__ __forceinline__ unsigned long long pack64(unsigned s, unsigned c)
 {
     return ((unsigned long long)c << 32) | (unsigned long long)s;
 }
 
-// Target of a run: the CTA's shared box (sum and count words) or, in direct
-// mode, the packed HBM accumulators.
-struct Target {
-    unsigned *bsum;
-    unsigned *bcnt;
-    unsigned long long *acc;
-};
-
-template <bool SHARED>
-__device__ __forceinline__ void add_run(const Target &t, unsigned key, unsigned s, unsigned c)
+// One pixel: box-local voxel from the coordinates, then the accumulate.
+template <bool CHECK, int MODE>
+__device__ __forceinline__ void put(unsigned *box, unsigned cap, unsigned long long *acc,
+                                    long long qx, long long qy, long long qz, unsigned ex,
+                                    unsigned ey, unsigned ez, unsigned I)
 {
-    if (SHARED) {
-        atomicAdd(t.bsum + key, s);
-        atomicAdd(t.bcnt + key, c);
+    const unsigned lx = (unsigned)hi32(qx), ly = (unsigned)hi32(qy), lz = (unsigned)hi32(qz);
+    if (CHECK && !(lx < ex && ly < ey && lz < ez))
+        return;
+    const unsigned key = (lz * ey + ly) * ex + lx;
+    if (MODE == MODE_PACKED) {
+        atomicAdd(box + key, (1u << kCountShift) | I);
+    } else if (MODE == MODE_SPLIT) {
+        atomicAdd(box + key, I);
+        atomicAdd(box + cap + key, 1u);
     } else {
-        atomicAdd(t.acc + key, pack(s, c));
+        atomicAdd(acc + key, pack64(I, 1u));
     }
 }
 
-// Walk one run of up to 16 pixels along a row.  q*: box-local Q31.32
-// coordinates (+2^31 already applied) of the first pixel; a*: per-column
-// steps.  Key = box-local linear index (ex*ey*ez box), or kOut.
-template <bool VEC, bool CHECK, bool SHARED>
-__device__ __forceinline__ void walk_chunk(const uint32_t (&pw)[4], int npx, long long qx,
-                                           long long qy, long long qz, long long ax, long long ay,
-                                           long long az, unsigned ex, unsigned ey, unsigned ez,
-                                           const Target &t)
+template <bool VEC, bool CHECK, int MODE>
+__device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1,
+                                           int v0, int v1, const long long (&off)[3],
+                                           unsigned ex, unsigned ey, unsigned ez, unsigned *box,
+                                           unsigned cap)
 {
-    unsigned cur = kNone, rs = 0;
-    int start = 0;
-#pragma unroll
-    for (int p = 0; p < 16; ++p) {
-        if (!VEC && p >= npx)
-            break;
-        const int lx = hi32(qx), ly = hi32(qy), lz = hi32(qz);
-        unsigned key;
-        if (CHECK) {
-            const bool in = (unsigned)lx < ex && (unsigned)ly < ey && (unsigned)lz < ez;
-            key = in ? ((unsigned)lz * ey + (unsigned)ly) * ex + (unsigned)lx : kOut;
-        } else {
-            key = ((unsigned)lz * ey + (unsigned)ly) * ex + (unsigned)lx;
-        }
-        if (key != cur) {
-            if (p != 0 && cur != kOut)
-                add_run<SHARED>(t, cur, rs, (unsigned)(p - start));
-            cur = key;
-            rs = 0;
-            start = p;
-        }
-        rs += (pw[p >> 2] >> (8 * (p & 3))) & 0xFFu;
-        qx += ax;
-        qy += ay;
-        qz += az;
-    }
-    if (cur != kOut)
-        add_run<SHARED>(t, cur, rs, (unsigned)((VEC ? 16 : npx) - start));
-}
-
-template <bool VEC, bool CHECK, bool SHARED>
-__device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1, int v0, int v1,
-                           const long long (&off)[3], unsigned ex, unsigned ey, unsigned ez,
-                           const Target &target)
-{
-    const int cpr = (u1 - u0 + 15) >> 4;  // chunks per row
-    const int nchunks = cpr * (v1 - v0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int u = u0 + 4 * lane;
+    if (u >= u1)
+        return;
+    const int npx = min(4, u1 - u);
     for (int f = f0; f < f1; ++f) {
         const FrameRec *r = a.rec + f;
         if (!r->valid)
             continue;
         const long long Ax = r->q[0], Ay = r->q[1], Az = r->q[2];
         const long long Bx = r->q[3], By = r->q[4], Bz = r->q[5];
-        const long long Cx = r->q[6] + off[0], Cy = r->q[7] + off[1], Cz = r->q[8] + off[2];
-        const uint8_t *img = a.img + (size_t)f * a.H * a.W;
-        for (int k = threadIdx.x; k < nchunks; k += kThreads) {
-            const int row = k / cpr;
-            const int u = u0 + ((k - row * cpr) << 4);
-            const int v = v0 + row;
-            const uint8_t *src = img + (size_t)v * a.W + u;
-            uint32_t pw[4];
-            int npx = 16;
+        // step from (u+3, v) to (u, v + kWarps)
+        const long long Sx = kWarps * Bx - 3 * Ax, Sy = kWarps * By - 3 * Ay,
+                        Sz = kWarps * Bz - 3 * Az;
+        int v = v0 + warp;
+        long long qx = r->q[6] + off[0] + (long long)u * Ax + (long long)v * Bx;
+        long long qy = r->q[7] + off[1] + (long long)u * Ay + (long long)v * By;
+        long long qz = r->q[8] + off[2] + (long long)u * Az + (long long)v * Bz;
+        const uint8_t *src = a.img + ((size_t)f * a.H + v) * a.W + u;
+        const size_t rstep = (size_t)kWarps * a.W;
+        for (; v < v1; v += kWarps, src += rstep) {
+            uint32_t w;
             if (VEC) {
-                const uint4 q = __ldcs(reinterpret_cast<const uint4 *>(src));
-                pw[0] = q.x;
-                pw[1] = q.y;
-                pw[2] = q.z;
-                pw[3] = q.w;
+                w = __ldcs(reinterpret_cast<const unsigned *>(src));
             } else {
-                npx = min(16, u1 - u);
-                pw[0] = pw[1] = pw[2] = pw[3] = 0;
+                w = 0;
                 for (int p = 0; p < npx; ++p)
-                    pw[p >> 2] |= (uint32_t)__ldcs(src + p) << (8 * (p & 3));
+                    w |= (uint32_t)__ldcs(src + p) << (8 * p);
             }
-            const long long qx = Cx + (long long)u * Ax + (long long)v * Bx;
-            const long long qy = Cy + (long long)u * Ay + (long long)v * By;
-            const long long qz = Cz + (long long)u * Az + (long long)v * Bz;
-            walk_chunk<VEC, CHECK, SHARED>(pw, npx, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, target);
+            put<CHECK, MODE>(box, cap, a.acc, qx, qy, qz, ex, ey, ez, w & 0xFFu);
+            if (VEC || npx > 1)
+                put<CHECK, MODE>(box, cap, a.acc, qx + Ax, qy + Ay, qz + Az, ex, ey, ez,
+                                 (w >> 8) & 0xFFu);
+            if (VEC || npx > 2)
+                put<CHECK, MODE>(box, cap, a.acc, qx + 2 * Ax, qy + 2 * Ay, qz + 2 * Az, ex, ey,
+                                 ez, (w >> 16) & 0xFFu);
+            qx += 3 * Ax;
+            qy += 3 * Ay;
+            qz += 3 * Az;
+            if (VEC || npx > 3)
+                put<CHECK, MODE>(box, cap, a.acc, qx, qy, qz, ex, ey, ez, w >> 24);
+            qx += Sx;
+            qy += Sy;
+            qz += Sz;
         }
     }
 }
@@ -155,98 +137,126 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
 template <bool VEC>
 __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
 {
-    extern __shared__ unsigned box[];  // [box_cap] sums, then [box_cap] counts
+    extern __shared__ unsigned box[];
     __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int u0 = tx * a.twc * 16, v0 = ty * a.th;
-    const int u1 = min(a.W, u0 + a.twc * 16), v1 = min(a.H, v0 + a.th);
+    const int u0 = tx * kTileW, v0 = ty * a.th;
+    const int u1 = min(a.W, u0 + kTileW), v1 = min(a.H, v0 + a.th);
     const int f0 = blockIdx.y * a.fpc, f1 = min(a.n, f0 + a.fpc);
 
-    if (threadIdx.x == 0) {
-        long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
-        long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-        bool any = false;
-        for (int f = f0; f < f1; ++f) {
+    if (threadIdx.x < 32) {
+        // lane i: corner i & 3 of frame f0 + (i >> 2) (up to 8 frames)
+        const int lane = threadIdx.x;
+        const int f = f0 + (lane >> 2);
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        int cnt = 0, valid = 0;
+        if (f < f1 && a.rec[f].valid) {
             const FrameRec *r = a.rec + f;
-            if (!r->valid)
-                continue;
-            any = true;
-            for (int c = 0; c < 4; ++c) {
-                const long long u = (c & 1) ? u1 - 1 : u0;
-                const long long v = (c & 2) ? v1 - 1 : v0;
+            const long long u = (lane & 1) ? u1 - 1 : u0;
+            const long long v = (lane & 2) ? v1 - 1 : v0;
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const long long Q = r->q[6 + ax] + u * r->q[ax] + v * r->q[3 + ax];
+                lo[ax] = hi[ax] = (int)((Q + (1LL << 31)) >> 32);  // arithmetic: floor
+            }
+            valid = 1;
+            cnt = (lane & 3) == 0 ? r->nmax : 0;
+        }
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            lo[ax] = __reduce_min_sync(0xFFFFFFFFu, lo[ax]);
+            hi[ax] = __reduce_max_sync(0xFFFFFFFFu, hi[ax]);
+        }
+        const unsigned any = __reduce_or_sync(0xFFFFFFFFu, (unsigned)valid);
+        const unsigned nsum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
+        if (lane == 0) {
+            int mode = MODE_SKIP, check = 0;
+            if (any) {
+                const int n[3] = {a.nx, a.ny, a.nz};
+                long long vol = 1;
+                mode = MODE_PACKED;
                 for (int ax = 0; ax < 3; ++ax) {
-                    const long long Q = r->q[6 + ax] + u * r->q[ax] + v * r->q[3 + ax];
-                    const long long i = (Q + (1LL << 31)) >> 32;  // arithmetic: floor
-                    lo[ax] = min(lo[ax], i);
-                    hi[ax] = max(hi[ax], i);
+                    const int l = max(lo[ax], 0), h = min(hi[ax], n[ax] - 1);
+                    if (l > h)
+                        mode = MODE_SKIP;
+                    if (l != lo[ax] || h != hi[ax])
+                        check = 1;
+                    s_lo[ax] = l;
+                    s_ext[ax] = max(h - l + 1, 0);
+                    vol *= max(h - l + 1, 0);
+                }
+                if (mode != MODE_SKIP) {
+                    if (nsum <= kPackedMaxCount && vol <= kSmem / 4)
+                        mode = MODE_PACKED;
+                    else if (vol <= kSmem / 8)
+                        mode = MODE_SPLIT;
+                    else
+                        mode = MODE_DIRECT;
                 }
             }
+            s_mode = mode;
+            s_check = check;
         }
-        int mode = 0, check = 0;
-        if (any) {
-            const long long n[3] = {a.nx, a.ny, a.nz};
-            long long vol = 1;
-            mode = 1;
-            for (int ax = 0; ax < 3; ++ax) {
-                const long long l = max(lo[ax], 0LL), h = min(hi[ax], n[ax] - 1);
-                if (l > h)
-                    mode = 0;
-                if (l != lo[ax] || h != hi[ax])
-                    check = 1;
-                s_lo[ax] = (int)l;
-                s_ext[ax] = (int)max(h - l + 1, 0LL);
-                vol *= max(h - l + 1, 0LL);
-            }
-            if (mode == 1 && vol > a.box_cap)
-                mode = 2;
-        }
-        s_mode = mode;
-        s_check = check;
     }
     __syncthreads();
     const int mode = s_mode;
-    if (mode == 0)
+    if (mode == MODE_SKIP)
         return;
 
-    if (mode == 1) {
-        const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
-        const unsigned bvol = ex * ey * ez;
-        const Target t{box, box + a.box_cap, nullptr};
-        for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
-            t.bsum[i] = 0u;
-            t.bcnt[i] = 0u;
-        }
-        __syncthreads();
-        const long long off[3] = {(1LL << 31) - ((long long)s_lo[0] << 32),
-                                  (1LL << 31) - ((long long)s_lo[1] << 32),
-                                  (1LL << 31) - ((long long)s_lo[2] << 32)};
+    if (mode == MODE_DIRECT) {
+        // keys are global linear indices into the whole grid
+        const long long off[3] = {1LL << 31, 1LL << 31, 1LL << 31};
+        run_frames<VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
+                                           (unsigned)a.ny, (unsigned)a.nz, nullptr, 0);
+        return;
+    }
+    const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
+    const unsigned bvol = ex * ey * ez;
+    const unsigned cap = kSmem / 8;
+    for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
+        box[i] = 0u;
+        if (mode == MODE_SPLIT)
+            box[cap + i] = 0u;
+    }
+    __syncthreads();
+    const long long off[3] = {(1LL << 31) - ((long long)s_lo[0] << 32),
+                              (1LL << 31) - ((long long)s_lo[1] << 32),
+                              (1LL << 31) - ((long long)s_lo[2] << 32)};
+    if (mode == MODE_PACKED) {
         if (s_check)
-            run_frames<VEC, true, true>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, t);
+            run_frames<VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box, 0);
         else
-            run_frames<VEC, false, true>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, t);
-        __syncthreads();
-        // Flush: one warp per box row (fixed y, z), lanes along x.
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (unsigned row = warp; row < ey * ez; row += kThreads / 32) {
-            const unsigned ly = row % ey, lz = row / ey;
-            unsigned long long *dst =
-                a.acc + ((size_t)(lz + s_lo[2]) * a.ny + (ly + s_lo[1])) * a.nx + s_lo[0];
-            const unsigned *src_s = t.bsum + (size_t)row * ex;
-            const unsigned *src_c = t.bcnt + (size_t)row * ex;
-            for (unsigned lx = lane; lx < ex; lx += 32) {
-                const unsigned c = src_c[lx];
+            run_frames<VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
+                                                0);
+    } else {
+        if (s_check)
+            run_frames<VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
+                                              cap);
+        else
+            run_frames<VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
+                                               cap);
+    }
+    __syncthreads();
+    // Flush: one warp per box row (fixed y, z), lanes along x.
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (unsigned row = warp; row < ey * ez; row += kWarps) {
+        const unsigned ly = row % ey, lz = row / ey;
+        unsigned long long *dst =
+            a.acc + ((size_t)(lz + s_lo[2]) * a.ny + (ly + s_lo[1])) * a.nx + s_lo[0];
+        const unsigned *src = box + (size_t)row * ex;
+        for (unsigned lx = lane; lx < ex; lx += 32) {
+            const unsigned e = src[lx];
+            if (mode == MODE_PACKED) {
+                if (e != 0u)
+                    atomicAdd(dst + lx, pack64(e & ((1u << kCountShift) - 1), e >> kCountShift));
+            } else {
+                const unsigned c = src[cap + lx];
                 if (c != 0u)
-                    atomicAdd(dst + lx, pack(src_s[lx], c));
+                    atomicAdd(dst + lx, pack64(e, c));
             }
         }
-    } else {
-        // Direct mode: keys are global linear indices into the whole grid.
-        const long long off[3] = {1LL << 31, 1LL << 31, 1LL << 31};
-        const Target t{nullptr, nullptr, a.acc};
-        run_frames<VEC, true, false>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
-                                     (unsigned)a.ny, (unsigned)a.nz, t);
     }
 }
 
@@ -267,37 +277,19 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;
-    // Tile: 128 columns x 64 rows (smaller frames: the whole width / height).
-    a.twc = min(8, (W + 15) / 16);
     a.th = min(64, H);
-    a.tiles_x = (W + a.twc * 16 - 1) / (a.twc * 16);
-    a.tiles_y = (H + a.th - 1) / a.th;
-    a.fpc = 4;
-    const int smem = 48 * 1024;
-    a.box_cap = smem / 8;  // entries: one 32-bit sum + one 32-bit count each
-    const bool vec = (W % 16 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0);
+    a.tiles_x = (W + kTileW - 1) / kTileW;
+    const int tiles_y = (H + a.th - 1) / a.th;
+    a.fpc = 4;  // <= 8: warp 0 computes the box from 4 corners x up to 8 frames
+    const bool vec = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 3) == 0);
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
-    dim3 grid(a.tiles_x * a.tiles_y, (unsigned)groups);
-    // The box plus the CTA's few static words exceed the 48 KB default.
-    static int attr_device = -1;
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (attr_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_insert_pnn<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess)
-            return e;
-        attr_device = dev;
-    }
+    dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
     if (vec)
-        k_insert_pnn<true><<<grid, kThreads, smem, st>>>(a);
+        k_insert_pnn<true><<<grid, kThreads, kSmem, st>>>(a);
     else
-        k_insert_pnn<false><<<grid, kThreads, smem, st>>>(a);
+        k_insert_pnn<false><<<grid, kThreads, kSmem, st>>>(a);
     return cudaGetLastError();
 }
 

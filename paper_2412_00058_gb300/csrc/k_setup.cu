@@ -31,6 +31,32 @@ __device__ __forceinline__ long long q32_round(double x)
     return (long long)t;
 }
 
+// Upper bound on how many pixels of one frame can land in the same voxel.
+// Two such pixels differ by du*A + dv*B with every component in (-1, 1), so
+// |dv| < sqrt(3)|A| / |A x B| (the distance of B from the line of A) and,
+// within one row, at most ceil(1 / max_a |A_a|) columns fit in a unit
+// interval:  N <= (floor(sqrt(3)|A|/|AxB|) + 1) * ceil(1/|A|_inf).
+// Computed on the unquantised map with a 1e-6 relative margin (the
+// quantised map differs by < 2^-33 per entry, and the cross product is
+// trusted only when A and B are more than 1e-6 rad from parallel);
+// saturates at 2^20.
+__device__ int pixels_per_voxel_bound(const double *d)
+{
+    const double ax = d[0], ay = d[1], az = d[2], bx = d[3], by = d[4], bz = d[5];
+    const double cx = ay * bz - az * by, cy = az * bx - ax * bz, cz = ax * by - ay * bx;
+    const double det = sqrt(cx * cx + cy * cy + cz * cz);
+    const double na = sqrt(ax * ax + ay * ay + az * az);
+    const double nb = sqrt(bx * bx + by * by + bz * bz);
+    const double ninf = fmax(fabs(ax), fmax(fabs(ay), fabs(az)));
+    // nearly parallel A, B: the cross product loses relative accuracy
+    if (!(det > 1e-6 * na * nb) || !(ninf > 1e-9))
+        return 1 << 20;
+    const double rows = floor(1.7320508075688772 * na / det * (1.0 + 1e-6)) + 1.0;
+    const double cols = ceil(1.0 / ninf * (1.0 + 1e-6));
+    const double n = rows * cols;
+    return n >= 1048576.0 ? (1 << 20) : (int)n;
+}
+
 __global__ void k_frame_setup(const double *__restrict__ poses, int n, SetupParams sp,
                               FrameRec *__restrict__ rec, uint32_t *status)
 {
@@ -70,7 +96,8 @@ __global__ void k_frame_setup(const double *__restrict__ poses, int n, SetupPara
     for (int i = 0; i < 9; ++i)
         r.q[i] = ok ? q32_round(r.d[i]) : 0;
     r.valid = ok ? 1 : 0;
-    r.pad[0] = r.pad[1] = r.pad[2] = 0;
+    r.nmax = ok ? pixels_per_voxel_bound(r.d) : (1 << 20);
+    r.pad[0] = r.pad[1] = 0;
     rec[f] = r;
     if (!ok)
         atomicOr(status, USV_STATUS_BAD_POSE);

@@ -15,7 +15,8 @@ struct FrameRec {
     long long q[9];  // Q31.32 per-step map: A (per column), B (per row), C (pixel 0,0)
     double d[9];     // FP64 map; linear: same as q unquantised; convex: per-mm factors
     int valid;       // 0: frame skipped (bad pose)
-    int pad[3];
+    int nmax;        // upper bound on the pixels of this frame that share one voxel
+    int pad[2];
 };
 static_assert(sizeof(FrameRec) == 160, "FrameRec layout");
 
