@@ -112,6 +112,8 @@ __device__ __forceinline__ unsigned mean_round_small(unsigned S, unsigned C)
 
 __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
 {
+    constexpr int NT = FTX * FBY;
+    constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries copied per thread
     __shared__ __align__(16) unsigned long long P[FSLOTS][FPY][FPX];
     __shared__ uint2 R[FPY][FTX];
     const auto *acc = static_cast<const unsigned long long *>(a.acc);
@@ -120,17 +122,29 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
     const int z0 = blockIdx.z * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
     const int x = x0 + tx;
+    const size_t plane = (size_t)a.nx * a.ny;
     bool saturated = false;
 
+    // this thread's share of every plane copy: in-plane offsets + validity
+    size_t goff[PER];
+    bool gok[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        const int ly = i / FPX, lx = i - ly * FPX;
+        const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
+        gok[k] = i < FPLANE && X >= 0 && X < a.nx && Y >= 0 && Y < a.ny;
+        goff[k] = gok[k] ? (size_t)Y * a.nx + X : 0;
+    }
     auto issue = [&](int pl) {
         if (pl <= z1) {
             unsigned long long *dst = &P[(pl + FSLOTS) % FSLOTS][0][0];
-            for (int i = tid; i < FPLANE; i += FTX * FBY) {
-                const int ly = i / FPX, lx = i - ly * FPX;
-                const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
-                const bool ok = pl >= 0 && pl < a.nz && X >= 0 && X < a.nx && Y >= 0 && Y < a.ny;
-                cp_async8(dst + i, ok ? acc + ((size_t)pl * a.ny + Y) * a.nx + X : acc, ok);
-            }
+            const bool zok = pl >= 0 && pl < a.nz;
+            const unsigned long long *base = acc + (zok ? (size_t)pl * plane : 0);
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                if (tid + k * NT < FPLANE)
+                    cp_async8(dst + tid + k * NT, base + goff[k], zok && gok[k]);
         }
         cp_async_commit();
     };
@@ -149,16 +163,18 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
         const int slot = (pl + FSLOTS) % FSLOTS;
         const unsigned long long(*Pp)[FPX] = P[slot];
         bool nzp = false, bigp = false;
-        for (int i = tid; i < FPLANE; i += FTX * FBY) {
-            const unsigned long long w = (&Pp[0][0])[i];
-            nzp |= w != 0ull;
-            bigp |= (unsigned)w >= kBig || (unsigned)(w >> 32) >= kBig;
-        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (tid + k * NT < FPLANE) {
+                const unsigned long long w = (&Pp[0][0])[tid + k * NT];  // own copies: visible
+                nzp |= w != 0ull;
+                bigp |= (unsigned)w >= kBig || (unsigned)(w >> 32) >= kBig;
+            }
         const int nz_pl = __syncthreads_or(nzp);
         const int big_pl = nz_pl ? __syncthreads_or(bigp) : 0;
         uint2 Bn[2] = {make_uint2(0, 0), make_uint2(0, 0)};
         if (nz_pl && !big_pl) {
-            for (int i = tid; i < FPY * FTX; i += FTX * FBY) {
+            for (int i = tid; i < FPY * FTX; i += NT) {
                 const int ry = i / FTX, rx = i - ry * FTX;
                 const unsigned long long p0 = Pp[ry][rx], p1 = Pp[ry][rx + 1], p2 = Pp[ry][rx + 2];
                 R[ry][rx] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
@@ -198,27 +214,23 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
             const int y = y0 + ly;
             unsigned v = 0;
             bool has = false;
-            if (any) {
+            if (any && !big) {
                 const unsigned long long own = P[sz][ly + 1][tx + 1];
                 const unsigned c_own = (unsigned)(own >> 32);
-                if (!big) {
-                    if (c_own != 0u) {
-                        v = mean_round_small((unsigned)own, c_own);
-                        has = true;
-                    } else {
-                        // own count is 0; drop its sum too (only neighbours pool)
-                        const unsigned S = B[0][r].x + B[1][r].x + B[2][r].x - (unsigned)own;
-                        const unsigned C = B[0][r].y + B[1][r].y + B[2][r].y;
-                        has = C != 0u;
-                        if (has)
-                            v = mean_round_small(S, C);
-                    }
-                } else if (own >> 32) {
-                    saturated |= (own >> 32) >= (1ull << 24);
-                    v = mean_round_u8(own & 0xFFFFFFFFull, own >> 32);
-                    has = true;
-                } else {
-                    unsigned long long S = 0, C = 0;
+                // own samples if any, else the pooled neighbours (own count is
+                // 0 then; its sum is dropped so only neighbours pool)
+                const unsigned S = c_own ? (unsigned)own
+                                         : B[0][r].x + B[1][r].x + B[2][r].x - (unsigned)own;
+                const unsigned C = c_own ? c_own : B[0][r].y + B[1][r].y + B[2][r].y;
+                has = C != 0u;
+                if (has)
+                    v = mean_round_small(S, C);
+            } else if (any) {
+                const unsigned long long own = P[sz][ly + 1][tx + 1];
+                unsigned long long S = own & 0xFFFFFFFFull, C = own >> 32;
+                saturated |= C >= (1ull << 24);
+                if (C == 0) {
+                    S = 0ull - (own & 0xFFFFFFFFull);  // the centre is not a neighbour
 #pragma unroll
                     for (int dz = 0; dz < 3; ++dz) {
                         const int s2 = (z - 1 + dz + FSLOTS) % FSLOTS;
@@ -231,10 +243,10 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
                                 C += w >> 32;
                             }
                     }
-                    has = C != 0;
-                    if (has)
-                        v = mean_round_u8(S, C);
                 }
+                has = C != 0;
+                if (has)
+                    v = mean_round_u8(S, C);
             }
             const bool inside = x < a.nx && y < a.ny;
             if (inside)

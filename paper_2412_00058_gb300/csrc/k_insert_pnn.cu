@@ -6,16 +6,17 @@
 // integer, so the result is exact and independent of execution order.
 //
 // GB300 design:
-//  * one CTA = a tile of up to 128 columns x 64 rows of FPC consecutive
-//    frames; a warp covers one 128-pixel row segment, each lane four
-//    consecutive pixels read with one coalesced 32-bit load; warps take
-//    every 8th row;
+//  * one CTA = a tile of up to 256 columns x 32 rows of FPC consecutive
+//    frames; a warp covers one 256-pixel row segment, each lane eight
+//    consecutive pixels read with one coalesced 64-bit load (the next row's
+//    load is issued before the current row is processed); warps take every
+//    8th row;
 //  * the tile's voxel bounding box over its frames is exact (the map is
 //    affine, so the extremes sit at the tile corners), so the CTA can
 //    accumulate into a dense shared-memory box and then add each touched
 //    entry to HBM with one packed 64-bit global atomic;
 //  * per pixel: three exact 64-bit coordinate adds, the box index, one
-//    native 32-bit shared atomic.  In one step all 32 lanes handle pixels 4
+//    native 32-bit shared atomic.  In one step all 32 lanes handle pixels 8
 //    columns apart, i.e. (nearly always) different voxels, so the atomics
 //    neither diverge nor collide;
 //  * box entry layout: if the frames' bound on pixels per voxel (set-up
@@ -24,7 +25,9 @@
 //    two words (sum, count) -> two atomics; if the box does not fit in
 //    shared memory (pixels as coarse as voxels, steep poses) every pixel
 //    goes straight to an HBM atomic;
-//  * bounds checks run only in tiles whose box was clipped by the grid.
+//  * bounds checks run only in tiles whose box was clipped by the grid, and
+//    there once per 8-pixel group: along a row every voxel index is monotone,
+//    so a group whose two end pixels are inside the box is inside.
 #include <climits>
 
 #include "usv_internal.cuh"
@@ -35,7 +38,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kTileW = 128;          // columns per tile (32 lanes x 4 pixels)
+constexpr int kPix = 8;              // pixels per lane per row (one 64-bit load)
+constexpr int kTileW = 32 * kPix;    // columns per tile
 constexpr int kSmem = 32 * 1024;     // dynamic shared memory per CTA
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
 constexpr int kPackedMaxCount = 1023;
@@ -80,6 +84,24 @@ __device__ __forceinline__ void put(unsigned *box, unsigned cap, unsigned long l
     }
 }
 
+template <bool CHECK, int MODE>
+__device__ __forceinline__ void put_group(unsigned *box, unsigned cap, unsigned long long *acc,
+                                          long long qx, long long qy, long long qz, long long Ax,
+                                          long long Ay, long long Az, unsigned ex, unsigned ey,
+                                          unsigned ez, uint2 w, int npx)
+{
+#pragma unroll
+    for (int j = 0; j < kPix; ++j) {
+        if (j < npx) {
+            const unsigned word = j < 4 ? w.x : w.y;
+            put<CHECK, MODE>(box, cap, acc, qx, qy, qz, ex, ey, ez, (word >> (8 * (j & 3))) & 0xFFu);
+        }
+        qx += Ax;
+        qy += Ay;
+        qz += Az;
+    }
+}
+
 template <bool VEC, bool CHECK, int MODE>
 __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1,
                                            int v0, int v1, const long long (&off)[3],
@@ -87,49 +109,65 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
                                            unsigned cap)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int u = u0 + 4 * lane;
-    if (u >= u1)
+    const int u = u0 + kPix * lane;
+    if (u >= u1 || v0 + warp >= v1)
         return;
-    const int npx = min(4, u1 - u);
+    const int npx = VEC ? kPix : min(kPix, u1 - u);
+    const size_t rstep = (size_t)kWarps * a.W;
     for (int f = f0; f < f1; ++f) {
         const FrameRec *r = a.rec + f;
         if (!r->valid)
             continue;
         const long long Ax = r->q[0], Ay = r->q[1], Az = r->q[2];
         const long long Bx = r->q[3], By = r->q[4], Bz = r->q[5];
-        // step from (u+3, v) to (u, v + kWarps)
-        const long long Sx = kWarps * Bx - 3 * Ax, Sy = kWarps * By - 3 * Ay,
-                        Sz = kWarps * Bz - 3 * Az;
         int v = v0 + warp;
-        long long qx = r->q[6] + off[0] + (long long)u * Ax + (long long)v * Bx;
-        long long qy = r->q[7] + off[1] + (long long)u * Ay + (long long)v * By;
-        long long qz = r->q[8] + off[2] + (long long)u * Az + (long long)v * Bz;
+        const long long qx0 = r->q[6] + off[0] + (long long)u * Ax + (long long)v * Bx;
+        const long long qy0 = r->q[7] + off[1] + (long long)u * Ay + (long long)v * By;
+        const long long qz0 = r->q[8] + off[2] + (long long)u * Az + (long long)v * Bz;
+        const long long Rx = kWarps * Bx, Ry = kWarps * By, Rz = kWarps * Bz;  // row step
+        const long long Ex = (kPix - 1) * Ax, Ey = (kPix - 1) * Ay, Ez = (kPix - 1) * Az;
+        long long qx = qx0, qy = qy0, qz = qz0;
         const uint8_t *src = a.img + ((size_t)f * a.H + v) * a.W + u;
-        const size_t rstep = (size_t)kWarps * a.W;
-        for (; v < v1; v += kWarps, src += rstep) {
-            uint32_t w;
+        auto load = [&](const uint8_t *p) {
+            uint2 w;
             if (VEC) {
-                w = __ldcs(reinterpret_cast<const unsigned *>(src));
+                w = __ldcs(reinterpret_cast<const uint2 *>(p));
             } else {
-                w = 0;
-                for (int p = 0; p < npx; ++p)
-                    w |= (uint32_t)__ldcs(src + p) << (8 * p);
+                w = make_uint2(0u, 0u);
+                for (int j = 0; j < npx; ++j) {
+                    const unsigned b = __ldcs(p + j);
+                    if (j < 4)
+                        w.x |= b << (8 * j);
+                    else
+                        w.y |= b << (8 * (j - 4));
+                }
             }
-            put<CHECK, MODE>(box, cap, a.acc, qx, qy, qz, ex, ey, ez, w & 0xFFu);
-            if (VEC || npx > 1)
-                put<CHECK, MODE>(box, cap, a.acc, qx + Ax, qy + Ay, qz + Az, ex, ey, ez,
-                                 (w >> 8) & 0xFFu);
-            if (VEC || npx > 2)
-                put<CHECK, MODE>(box, cap, a.acc, qx + 2 * Ax, qy + 2 * Ay, qz + 2 * Az, ex, ey,
-                                 ez, (w >> 16) & 0xFFu);
-            qx += 3 * Ax;
-            qy += 3 * Ay;
-            qz += 3 * Az;
-            if (VEC || npx > 3)
-                put<CHECK, MODE>(box, cap, a.acc, qx, qy, qz, ex, ey, ez, w >> 24);
-            qx += Sx;
-            qy += Sy;
-            qz += Sz;
+            return w;
+        };
+        uint2 w = load(src);
+        for (; v < v1; v += kWarps) {
+            const bool more = v + kWarps < v1;
+            uint2 wn = make_uint2(0u, 0u);
+            if (more)
+                wn = load(src + rstep);
+            bool inside = true;
+            if (CHECK) {
+                const long long lx = qx + Ex, ly = qy + Ey, lz = qz + Ez;
+                inside = (unsigned)hi32(qx) < ex && (unsigned)hi32(qy) < ey &&
+                         (unsigned)hi32(qz) < ez && (unsigned)hi32(lx) < ex &&
+                         (unsigned)hi32(ly) < ey && (unsigned)hi32(lz) < ez;
+            }
+            if (!CHECK || inside)
+                put_group<false, MODE>(box, cap, a.acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w,
+                                       npx);
+            else
+                put_group<true, MODE>(box, cap, a.acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w,
+                                      npx);
+            qx += Rx;
+            qy += Ry;
+            qz += Rz;
+            src += rstep;
+            w = wn;
         }
     }
 }
@@ -277,11 +315,11 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;
-    a.th = min(64, H);
+    a.th = min(32, H);
     a.tiles_x = (W + kTileW - 1) / kTileW;
     const int tiles_y = (H + a.th - 1) / a.th;
     a.fpc = 4;  // <= 8: warp 0 computes the box from 4 corners x up to 8 frames
-    const bool vec = (W % 4 == 0) && ((reinterpret_cast<uintptr_t>(img) & 3) == 0);
+    const bool vec = (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
