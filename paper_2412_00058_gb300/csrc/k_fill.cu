@@ -62,26 +62,27 @@ __device__ __forceinline__ void load_plane(T (*pl)[PX], const T *acc, int z, con
 
 // ---- nearest-neighbour fill ------------------------------------------------
 //
-// CTA: 32 x 8 threads own a 32 x 16 (x, y) column tile (two rows per thread)
-// and march z.  Planes of packed accumulators (tile + 1-voxel halo) stream
-// into a 6-slot shared ring with cp.async, two planes ahead of use.  The
-// pooled 26-neighbour sums are separable: per plane, row sums over x
-// (shared), then 3x3 plane sums over y (registers, kept for three planes);
-// the 3x3x3 sum is the sum of three plane sums, own voxel included (an empty
-// voxel adds zero).  While every accumulator of the three planes is below
-// 2^26 (sum and count) the sums are exact in 32 bits; otherwise that plane
-// takes a direct 64-bit path.  Tiles whose three planes are all empty write
-// zeros without arithmetic.
-constexpr int FTX = 32, FTY = 16, FBY = 8;
+// CTA: 32 x 8 threads own a 32 x 32 (x, y) column tile; thread (tx, ty)
+// owns column x0 + tx, rows y0 + 4ty .. y0 + 4ty + 3, and the CTA marches z.
+// Planes of packed accumulators (tile + 1-voxel halo) stream into a 5-slot
+// shared ring with cp.async, two planes ahead of use.  The pooled sums are
+// separable: per plane each thread forms the x-row sums of its 6 rows
+// (y-1 .. y+4) and from them the 3x3 plane sums of its 4 voxels (registers,
+// kept for three planes); the 3x3x3 sum is the sum of three plane sums, own
+// voxel included (an empty voxel adds zero).  One OR over each plane tells
+// whether it is all zero (then the tile writes zeros without arithmetic) and
+// whether any accumulator reaches 2^26 (then that output plane takes a
+// direct 64-bit path); below 2^26 every sum is exact in 32 bits.
+constexpr int FTX = 32, FTY = 32, FBY = 8, FRW = 4;  // FRW rows per thread
 constexpr int FPX = FTX + 2, FPY = FTY + 2, FPLANE = FPX * FPY;
-constexpr int FSLOTS = 6;
+constexpr int FSLOTS = 5;
 constexpr unsigned kBig = 1u << 26;
+constexpr int kFillSmem = FSLOTS * FPLANE * 8;
 
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, bool valid)
+__device__ __forceinline__ void cp_async8(unsigned saddr, const void *gmem, bool valid)
 {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int n = valid ? 8 : 0;  // 0: zero-fill, nothing read
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(n)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(gmem), "r"(n)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -114,18 +115,18 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
 {
     constexpr int NT = FTX * FBY;
     constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries copied per thread
-    __shared__ __align__(16) unsigned long long P[FSLOTS][FPY][FPX];
-    __shared__ uint2 R[FPY][FTX];
+    extern __shared__ __align__(16) unsigned long long Pring[];  // [FSLOTS][FPY][FPX]
+    __shared__ unsigned sflag[FSLOTS];
     const auto *acc = static_cast<const unsigned long long *>(a.acc);
     auto *val = static_cast<uint8_t *>(a.val);
     const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
     const int z0 = blockIdx.z * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
-    const int x = x0 + tx;
+    const int x = x0 + tx, yb = 4 * ty;  // first of this thread's rows (tile-local)
     const size_t plane = (size_t)a.nx * a.ny;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(Pring);
     bool saturated = false;
 
-    // this thread's share of every plane copy: in-plane offsets + validity
     size_t goff[PER];
     bool gok[PER];
 #pragma unroll
@@ -138,60 +139,77 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
     }
     auto issue = [&](int pl) {
         if (pl <= z1) {
-            unsigned long long *dst = &P[(pl + FSLOTS) % FSLOTS][0][0];
+            const unsigned dst = sbase + (unsigned)(((pl + FSLOTS) % FSLOTS) * FPLANE * 8);
             const bool zok = pl >= 0 && pl < a.nz;
             const unsigned long long *base = acc + (zok ? (size_t)pl * plane : 0);
 #pragma unroll
             for (int k = 0; k < PER; ++k)
                 if (tid + k * NT < FPLANE)
-                    cp_async8(dst + tid + k * NT, base + goff[k], zok && gok[k]);
+                    cp_async8(dst + 8u * (tid + k * NT), base + goff[k], zok && gok[k]);
         }
         cp_async_commit();
     };
+    if (tid < FSLOTS)
+        sflag[tid] = 0u;
+    __syncthreads();
 
-    uint2 B[3][2];       // 3x3 plane sums (S, C) of planes z-1, z, z+1 for rows ty, ty+8
+    uint2 B[3][FRW];     // 3x3 plane sums (S, C) of planes z-1, z, z+1 for this thread's rows
     int nzf[3] = {0, 0, 0}, bigf[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
-        B[k][0] = B[k][1] = make_uint2(0, 0);
+#pragma unroll
+        for (int r = 0; r < FRW; ++r)
+            B[k][r] = make_uint2(0, 0);
+
+    // per-row output pointers, advanced one plane per output
+    const bool xin = x < a.nx;
+    size_t vrow = ((size_t)z0 * a.ny + y0 + yb) * a.nx + x;
+    size_t mrow = ((size_t)z0 * a.ny + y0 + yb) * a.nxw + blockIdx.x;
+    const size_t mplane = (size_t)a.ny * a.nxw;
 
     issue(z0 - 1);
     issue(z0);
+    int slot = (z0 - 1 + FSLOTS) % FSLOTS;
     for (int pl = z0 - 1; pl <= z1; ++pl) {
         issue(pl + 2);
         cp_async_wait<2>();
-        const int slot = (pl + FSLOTS) % FSLOTS;
-        const unsigned long long(*Pp)[FPX] = P[slot];
-        bool nzp = false, bigp = false;
+        const unsigned long long *Pp = Pring + slot * FPLANE;
+        unsigned orv = 0u;
 #pragma unroll
         for (int k = 0; k < PER; ++k)
             if (tid + k * NT < FPLANE) {
-                const unsigned long long w = (&Pp[0][0])[tid + k * NT];  // own copies: visible
-                nzp |= w != 0ull;
-                bigp |= (unsigned)w >= kBig || (unsigned)(w >> 32) >= kBig;
+                const unsigned long long w = Pp[tid + k * NT];  // own copies: visible
+                orv |= (unsigned)w | (unsigned)(w >> 32);
             }
-        const int nz_pl = __syncthreads_or(nzp);
-        const int big_pl = nz_pl ? __syncthreads_or(bigp) : 0;
-        uint2 Bn[2] = {make_uint2(0, 0), make_uint2(0, 0)};
+        orv = __reduce_or_sync(0xFFFFFFFFu, orv);
+        if (tx == 0 && orv)
+            atomicOr(&sflag[slot], orv);
+        __syncthreads();
+        const unsigned fl = sflag[slot];
+        if (tid == 0)
+            sflag[(slot + FSLOTS - 1) % FSLOTS] = 0u;  // read by everyone last iteration
+        const int nz_pl = fl != 0u, big_pl = fl >= kBig;
+        uint2 Bn[FRW];
+#pragma unroll
+        for (int r = 0; r < FRW; ++r)
+            Bn[r] = make_uint2(0, 0);
         if (nz_pl && !big_pl) {
-            for (int i = tid; i < FPY * FTX; i += NT) {
-                const int ry = i / FTX, rx = i - ry * FTX;
-                const unsigned long long p0 = Pp[ry][rx], p1 = Pp[ry][rx + 1], p2 = Pp[ry][rx + 2];
-                R[ry][rx] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
-                                       (unsigned)(p0 >> 32) + (unsigned)(p1 >> 32) +
-                                           (unsigned)(p2 >> 32));
-            }
-            __syncthreads();
+            uint2 Rw[FRW + 2];
 #pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const int ly = ty + r * FBY;
-                const uint2 a0 = R[ly][tx], a1 = R[ly + 1][tx], a2 = R[ly + 2][tx];
-                Bn[r] = make_uint2(a0.x + a1.x + a2.x, a0.y + a1.y + a2.y);
+            for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 -> halo rows yb .. yb+5
+                const unsigned long long *row = Pp + (yb + k) * FPX + tx;
+                const unsigned long long p0 = row[0], p1 = row[1], p2 = row[2];
+                Rw[k] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
+                                   (unsigned)(p0 >> 32) + (unsigned)(p1 >> 32) +
+                                       (unsigned)(p2 >> 32));
             }
+#pragma unroll
+            for (int r = 0; r < FRW; ++r)
+                Bn[r] = make_uint2(Rw[r].x + Rw[r + 1].x + Rw[r + 2].x,
+                                   Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
         }
-        // rotate: B[0] <- z-1, B[1] <- z, B[2] <- z+1 for output z = pl - 1
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
+        for (int r = 0; r < FRW; ++r) {
             B[0][r] = B[1][r];
             B[1][r] = B[2][r];
             B[2][r] = Bn[r];
@@ -203,58 +221,60 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
         bigf[1] = bigf[2];
         bigf[2] = big_pl;
         const int z = pl - 1;
-        if (z < z0)
-            continue;
-        const int sz = (z + FSLOTS) % FSLOTS;
-        const bool any = nzf[0] | nzf[1] | nzf[2];
-        const bool big = bigf[0] | bigf[1] | bigf[2];
+        if (z >= z0) {
+            const int sz = (slot + FSLOTS - 1) % FSLOTS;  // plane z
+            const unsigned long long *Pz = Pring + sz * FPLANE;
+            const bool any = nzf[0] | nzf[1] | nzf[2];
+            const bool big = bigf[0] | bigf[1] | bigf[2];
 #pragma unroll
-        for (int r = 0; r < 2; ++r) {
-            const int ly = ty + r * FBY;
-            const int y = y0 + ly;
-            unsigned v = 0;
-            bool has = false;
-            if (any && !big) {
-                const unsigned long long own = P[sz][ly + 1][tx + 1];
-                const unsigned c_own = (unsigned)(own >> 32);
-                // own samples if any, else the pooled neighbours (own count is
-                // 0 then; its sum is dropped so only neighbours pool)
-                const unsigned S = c_own ? (unsigned)own
-                                         : B[0][r].x + B[1][r].x + B[2][r].x - (unsigned)own;
-                const unsigned C = c_own ? c_own : B[0][r].y + B[1][r].y + B[2][r].y;
-                has = C != 0u;
-                if (has)
-                    v = mean_round_small(S, C);
-            } else if (any) {
-                const unsigned long long own = P[sz][ly + 1][tx + 1];
-                unsigned long long S = own & 0xFFFFFFFFull, C = own >> 32;
-                saturated |= C >= (1ull << 24);
-                if (C == 0) {
-                    S = 0ull - (own & 0xFFFFFFFFull);  // the centre is not a neighbour
-#pragma unroll
-                    for (int dz = 0; dz < 3; ++dz) {
-                        const int s2 = (z - 1 + dz + FSLOTS) % FSLOTS;
-#pragma unroll
-                        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                            for (int dx = 0; dx < 3; ++dx) {
-                                const unsigned long long w = P[s2][ly + dy][tx + dx];
-                                S += w & 0xFFFFFFFFull;
-                                C += w >> 32;
-                            }
+            for (int r = 0; r < FRW; ++r) {
+                const int y = y0 + yb + r;
+                unsigned v = 0;
+                bool has = false;
+                if (any && !big) {
+                    const unsigned long long own = Pz[(yb + r + 1) * FPX + tx + 1];
+                    const unsigned c_own = (unsigned)(own >> 32);
+                    // own samples if any, else the pooled neighbours (the own
+                    // count is 0 then; its sum is dropped so only neighbours pool)
+                    const unsigned S = c_own ? (unsigned)own
+                                             : B[0][r].x + B[1][r].x + B[2][r].x - (unsigned)own;
+                    const unsigned C = c_own ? c_own : B[0][r].y + B[1][r].y + B[2][r].y;
+                    has = C != 0u;
+                    if (has)
+                        v = mean_round_small(S, C);
+                } else if (any) {
+                    const unsigned long long own = Pz[(yb + r + 1) * FPX + tx + 1];
+                    unsigned long long S = own & 0xFFFFFFFFull, C = own >> 32;
+                    saturated |= C >= (1ull << 24);
+                    if (C == 0) {
+                        S = 0ull - (own & 0xFFFFFFFFull);  // the centre is not a neighbour
+                        for (int dz = 0; dz < 3; ++dz) {
+                            const unsigned long long *Pd =
+                                Pring + ((sz + FSLOTS - 1 + dz) % FSLOTS) * FPLANE;
+                            for (int dy = 0; dy < 3; ++dy)
+                                for (int dx = 0; dx < 3; ++dx) {
+                                    const unsigned long long w = Pd[(yb + r + dy) * FPX + tx + dx];
+                                    S += w & 0xFFFFFFFFull;
+                                    C += w >> 32;
+                                }
+                        }
                     }
+                    has = C != 0;
+                    if (has)
+                        v = mean_round_u8(S, C);
                 }
-                has = C != 0;
-                if (has)
-                    v = mean_round_u8(S, C);
+                const bool yin = y < a.ny;
+                if (xin && yin)
+                    val[vrow + (size_t)r * a.nx] = (uint8_t)v;
+                const unsigned bits = __ballot_sync(0xFFFFFFFFu, xin && yin && has);
+                if (tx == 0 && yin)
+                    a.mask[mrow + (size_t)r * a.nxw] = bits;
             }
-            const bool inside = x < a.nx && y < a.ny;
-            if (inside)
-                val[((size_t)z * a.ny + y) * a.nx + x] = (uint8_t)v;
-            const unsigned bits = __ballot_sync(0xFFFFFFFFu, inside && has);
-            if (tx == 0 && y < a.ny)
-                a.mask[((size_t)z * a.ny + y) * a.nxw + blockIdx.x] = bits;
+            vrow += plane;
+            mrow += mplane;
         }
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
+        __syncthreads();  // ring slot reuse
     }
     cp_async_wait<0>();
     if (__syncthreads_or(saturated) && tid == 0)
@@ -331,14 +351,24 @@ cudaError_t launch_fill_pnn(const Volume &v, cudaStream_t st)
 {
     FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0};
     const int gx = (v.g.nx + FTX - 1) / FTX, gy = (v.g.ny + FTY - 1) / FTY;
-    // ~6 waves of 6 resident CTAs per SM; slabs of at least 24 planes
-    const long long want = (long long)v.num_sms * 6 * 6;
+    // ~6 waves of 4 resident CTAs per SM; slabs of at least 16 planes
+    const long long want = (long long)v.num_sms * 4 * 6;
     long long zc = ((long long)gx * gy * v.g.nz + want - 1) / want;
-    zc = zc < 24 ? 24 : zc;
+    zc = zc < 16 ? 16 : zc;
     zc = zc > v.g.nz ? v.g.nz : zc;
     a.zchunk = (int)zc;
+    static int attr_device = -1;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_fill_pnn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFillSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_device = dev;
+    }
     const dim3 grid(gx, gy, (v.g.nz + a.zchunk - 1) / a.zchunk);
-    k_fill_pnn<<<grid, dim3(FTX, FBY), 0, st>>>(a);
+    k_fill_pnn<<<grid, dim3(FTX, FBY), kFillSmem, st>>>(a);
     return cudaGetLastError();
 }
 
