@@ -71,12 +71,13 @@ __device__ __forceinline__ void load_plane(T (*pl)[PX], const T *acc, int z, con
 // kept for three planes); the 3x3x3 sum is the sum of three plane sums, own
 // voxel included (an empty voxel adds zero).  One OR over each plane tells
 // whether it is all zero (then the tile writes zeros without arithmetic) and
-// whether any accumulator reaches 2^26 (then that output plane takes a
-// direct 64-bit path); below 2^26 every sum is exact in 32 bits.
+// whether any accumulator reaches 2^24 (then that output plane takes a
+// direct 64-bit path); below 2^24 every sum, and the mean's 2S + C, is exact
+// in 32 bits.
 constexpr int FTX = 32, FTY = 32, FBY = 8, FRW = 4;  // FRW rows per thread
 constexpr int FPX = FTX + 2, FPY = FTY + 2, FPLANE = FPX * FPY;
 constexpr int FSLOTS = 5;
-constexpr unsigned kBig = 1u << 26;
+constexpr unsigned kBig = 1u << 24;
 constexpr int kFillSmem = FSLOTS * FPLANE * 8;
 
 __device__ __forceinline__ void cp_async8(unsigned saddr, const void *gmem, bool valid)
@@ -89,26 +90,18 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// floor(S/C + 1/2) clamped to 255 for C > 0, S < 2^31, C < 2^31: an FP32
-// estimate of S/C is within one of floor(S/C); one exact integer correction
-// in each direction, then round half up from the exact remainder.
-__device__ __forceinline__ unsigned mean_round_small(unsigned S, unsigned C)
+// floor(S/C + 1/2) = floor((2S + C) / 2C), clamped to 255, for S < 2^29 and
+// 0 < C < 2^29 (so N = 2S + C and D = 2C fit in 31 bits): the FP32 estimate
+// of N/D is within one of the true quotient (|error| < 2^-21 relative, the
+// quotient is small), and the exact remainder N - q*D corrects it by one
+// in either direction.  Branch-free.
+__device__ __forceinline__ unsigned mean_round_fast(unsigned S, unsigned C)
 {
-    const float qf = __fdividef(__uint2float_rn(S), __uint2float_rn(C));
-    if (qf >= 254.5f)
-        return (unsigned long long)S >= 255ull * C ? 255u : mean_round_u8(S, C);
-    unsigned q = (unsigned)qf;
-    unsigned long long qc = (unsigned long long)q * C;
-    if (qc > S) {
-        --q;
-        qc -= C;
-    } else if (qc + C <= S) {
-        ++q;
-        qc += C;
-    }
-    const unsigned r = S - (unsigned)qc;
-    q += (2u * r >= C) ? 1u : 0u;
-    return q > 255u ? 255u : q;
+    const unsigned N = 2u * S + C, D = 2u * C;
+    unsigned q = (unsigned)__fdividef(__uint2float_rn(N), __uint2float_rn(D));
+    const int r = (int)(N - q * D);
+    q = q + (r >= (int)D ? 1u : 0u) - (r < 0 ? 1u : 0u);
+    return min(q, 255u);
 }
 
 __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
@@ -153,7 +146,9 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
         sflag[tid] = 0u;
     __syncthreads();
 
-    uint2 B[3][FRW];     // 3x3 plane sums (S, C) of planes z-1, z, z+1 for this thread's rows
+    // 3x3 plane sums (S, C) of this thread's rows; plane p lives in slot p % 3
+    // (the 3x3x3 sum adds all three, so the order does not matter)
+    uint2 B[3][FRW];
     int nzf[3] = {0, 0, 0}, bigf[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -161,16 +156,14 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
         for (int r = 0; r < FRW; ++r)
             B[k][r] = make_uint2(0, 0);
 
-    // per-row output pointers, advanced one plane per output
+    // output pointers of this thread's first row, advanced one plane per output
     const bool xin = x < a.nx;
-    size_t vrow = ((size_t)z0 * a.ny + y0 + yb) * a.nx + x;
-    size_t mrow = ((size_t)z0 * a.ny + y0 + yb) * a.nxw + blockIdx.x;
+    uint8_t *vout = val + ((size_t)z0 * a.ny + y0 + yb) * a.nx + x;
+    uint32_t *mout = a.mask + ((size_t)z0 * a.ny + y0 + yb) * a.nxw + blockIdx.x;
     const size_t mplane = (size_t)a.ny * a.nxw;
+    const int nrows = min(FRW, a.ny - (y0 + yb));  // rows of this thread inside the grid
 
-    issue(z0 - 1);
-    issue(z0);
-    int slot = (z0 - 1 + FSLOTS) % FSLOTS;
-    for (int pl = z0 - 1; pl <= z1; ++pl) {
+    auto step = [&](int pl, int slot, uint2(&Bn)[FRW], int &nzn, int &bign) {
         issue(pl + 2);
         cp_async_wait<2>();
         const unsigned long long *Pp = Pring + slot * FPLANE;
@@ -187,16 +180,16 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
         __syncthreads();
         const unsigned fl = sflag[slot];
         if (tid == 0)
-            sflag[(slot + FSLOTS - 1) % FSLOTS] = 0u;  // read by everyone last iteration
-        const int nz_pl = fl != 0u, big_pl = fl >= kBig;
-        uint2 Bn[FRW];
+            sflag[slot == 0 ? FSLOTS - 1 : slot - 1] = 0u;  // read by everyone last step
+        nzn = fl != 0u;
+        bign = fl >= kBig;
 #pragma unroll
         for (int r = 0; r < FRW; ++r)
             Bn[r] = make_uint2(0, 0);
-        if (nz_pl && !big_pl) {
+        if (nzn && !bign) {
             uint2 Rw[FRW + 2];
 #pragma unroll
-            for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 -> halo rows yb .. yb+5
+            for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 = halo rows yb .. yb+5
                 const unsigned long long *row = Pp + (yb + k) * FPX + tx;
                 const unsigned long long p0 = row[0], p1 = row[1], p2 = row[2];
                 Rw[k] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
@@ -208,27 +201,14 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
                 Bn[r] = make_uint2(Rw[r].x + Rw[r + 1].x + Rw[r + 2].x,
                                    Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
         }
-#pragma unroll
-        for (int r = 0; r < FRW; ++r) {
-            B[0][r] = B[1][r];
-            B[1][r] = B[2][r];
-            B[2][r] = Bn[r];
-        }
-        nzf[0] = nzf[1];
-        nzf[1] = nzf[2];
-        nzf[2] = nz_pl;
-        bigf[0] = bigf[1];
-        bigf[1] = bigf[2];
-        bigf[2] = big_pl;
         const int z = pl - 1;
         if (z >= z0) {
-            const int sz = (slot + FSLOTS - 1) % FSLOTS;  // plane z
+            const int sz = slot == 0 ? FSLOTS - 1 : slot - 1;  // plane z
             const unsigned long long *Pz = Pring + sz * FPLANE;
             const bool any = nzf[0] | nzf[1] | nzf[2];
             const bool big = bigf[0] | bigf[1] | bigf[2];
 #pragma unroll
             for (int r = 0; r < FRW; ++r) {
-                const int y = y0 + yb + r;
                 unsigned v = 0;
                 bool has = false;
                 if (any && !big) {
@@ -240,8 +220,7 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
                                              : B[0][r].x + B[1][r].x + B[2][r].x - (unsigned)own;
                     const unsigned C = c_own ? c_own : B[0][r].y + B[1][r].y + B[2][r].y;
                     has = C != 0u;
-                    if (has)
-                        v = mean_round_small(S, C);
+                    v = mean_round_fast(S, has ? C : 1u);
                 } else if (any) {
                     const unsigned long long own = Pz[(yb + r + 1) * FPX + tx + 1];
                     unsigned long long S = own & 0xFFFFFFFFull, C = own >> 32;
@@ -263,18 +242,34 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
                     if (has)
                         v = mean_round_u8(S, C);
                 }
-                const bool yin = y < a.ny;
+                const bool yin = r < nrows;
                 if (xin && yin)
-                    val[vrow + (size_t)r * a.nx] = (uint8_t)v;
+                    vout[(size_t)r * a.nx] = (uint8_t)v;
                 const unsigned bits = __ballot_sync(0xFFFFFFFFu, xin && yin && has);
                 if (tx == 0 && yin)
-                    a.mask[mrow + (size_t)r * a.nxw] = bits;
+                    mout[(size_t)r * a.nxw] = bits;
             }
-            vrow += plane;
-            mrow += mplane;
+            vout += plane;
+            mout += mplane;
         }
-        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
         __syncthreads();  // ring slot reuse
+    };
+
+    issue(z0 - 1);
+    issue(z0);
+    int slot = (z0 - 1 + FSLOTS) % FSLOTS;
+    // plane p's sums go to B[(p - z0 + 1) % 3]; unrolled by 3 so the slot is static
+    for (int pl = z0 - 1; pl <= z1; pl += 3) {
+        step(pl, slot, B[0], nzf[0], bigf[0]);
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
+        if (pl + 1 > z1)
+            break;
+        step(pl + 1, slot, B[1], nzf[1], bigf[1]);
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
+        if (pl + 2 > z1)
+            break;
+        step(pl + 2, slot, B[2], nzf[2], bigf[2]);
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
     }
     cp_async_wait<0>();
     if (__syncthreads_or(saturated) && tid == 0)
