@@ -173,6 +173,39 @@ int usv_project_depth_band(usv_volume *vol, int32_t z_lo, int32_t z_hi, float *o
 int usv_volume_read(usv_volume *vol, int32_t what, void *dst_dev, void *stream);
 int usv_volume_write_accum(usv_volume *vol, const void *src_dev, void *stream);
 
+/* ------------------------------------------------------------------------
+ * usv_insert_pnn_noalloc -- nearest-neighbour insertion that allocates no
+ * memory at all.  The paper has no counterpart: this serves callers that
+ * cannot allocate device memory on the path that feeds frames (a real-time
+ * acquisition loop whose memory is fixed before the scan -- an allocation
+ * can block and synchronise the device mid-scan --, a deployment that
+ * forbids allocation after start-up, a plugin whose host framework owns
+ * every buffer), so they cannot provide the storage usv_volume_create()
+ * takes.  The result is bit-identical to usv_insert_frames() in USV_PNN.
+ *   accum_dev   [nz][ny][nx] uint64 packed accumulators (low 32 bits sum,
+ *               high 32 bits count, the USV_READ_ACCUM layout), owned by the
+ *               caller, 8-byte aligned; zero it to start a scan.
+ *   grid, spacing_mm, origin_mm   as for usv_volume_create().
+ *   images_dev, n, H, W, poses_dev, cal   as for usv_insert_frames(),
+ *               uint8 frames of a linear probe.
+ *   status_dev  optional device word: USV_STATUS_* bits are OR-ed into it
+ *               (clear it first); NULL: not reported.
+ * Its scratch (per-frame set-up records) is a fixed array inside the
+ * library sized for USV_NOALLOC_MAX_FRAMES frames (about 160 KB that every
+ * GPU which loads the library keeps until the process exits); n beyond that
+ * returns USV_ERR_RANGE -- split larger batches.  The first call on each
+ * device looks up the array's device address; make that first call before
+ * any stream capture.  All calls on one device share the array, so calls
+ * that overlap on the GPU (unordered streams) race: order them on one
+ * stream.  Nothing in the array has to start at zero: every call writes the
+ * records it reads.  Asynchronous on `stream` like the other calls.
+ * ---------------------------------------------------------------------- */
+#define USV_NOALLOC_MAX_FRAMES 1024
+int usv_insert_pnn_noalloc(uint64_t *accum_dev, usv_grid grid, const double spacing_mm[3],
+                           const double origin_mm[3], const void *images_dev, int32_t n,
+                           int32_t H, int32_t W, const double *poses_dev,
+                           const usv_calibration *cal, uint32_t *status_dev, void *stream);
+
 /* Synchronise `stream`, then return the device status bits (>= 0) and clear
  * them, or a negative USV_ERR_* code. */
 int usv_status(usv_volume *vol, void *stream);

@@ -33,7 +33,7 @@ READ_ACCUM, READ_VALUES, READ_MASK = 0, 1, 2
 EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_volume_reset",
            "usv_insert_frames", "usv_fill_holes", "usv_project_depth_band", "usv_volume_read",
            "usv_volume_write_accum", "usv_status", "usv_strerror", "usv_last_cuda_error",
-           "usv_abi_version")
+           "usv_abi_version", "usv_insert_pnn_noalloc")
 
 
 class UsvError(RuntimeError):
