@@ -174,6 +174,27 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def recorded_traffic(kernel_file: str = "paper_2412_00058_gb300/csrc/k_insert_pnn.cu",
+                     record: str = "profiles/insert_pnn_whole_spine_traffic.txt"):
+    """DRAM bytes per launch of the insertion kernel from the committed ncu
+    record, or None if the kernel source changed since it was taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, kernel_file), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+        kv = {}
+        with open(os.path.join(ROOT, record)) as f:
+            for line in f:
+                if "=" in line and not line.lstrip().startswith("#"):
+                    k, v = line.split("=", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------- workload
 
 def sweep_workload(frames: int = 3600):
@@ -419,7 +440,9 @@ def run_gpu(args):
             "stage_ms": {"insert": ins_ms, "fill": fill_ms, "project": proj_ms,
                          "reset_and_gaps": ms_per_step - ins_ms - fill_ms - proj_ms},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "insert (PNN)",
+                         "frac": achieved / peak,
+                         "traffic": recorded_traffic() if args.frames >= 3600 else None,
+                         "kernel": "insert (PNN)",
                          "algorithmic_bytes": ins_bytes, "peak_kind": peak_kind},
             "pipeline_roofline": {"algorithmic_bytes_per_step": step_bytes,
                                   "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
