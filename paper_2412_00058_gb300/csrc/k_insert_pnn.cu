@@ -40,7 +40,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPix = 8;              // pixels per lane per row (one 64-bit load)
 constexpr int kTileW = 32 * kPix;    // columns per tile
-constexpr int kSmem = 32 * 1024;     // dynamic shared memory per CTA
+constexpr int kSmem = 48 * 1024;     // dynamic shared memory per CTA (the box)
+constexpr int kFpc = 8;              // frames per CTA (<= 8: warp 0 takes 4 corners x 8 frames)
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
 constexpr int kPackedMaxCount = 1023;
 
@@ -106,7 +107,7 @@ template <bool VEC, bool CHECK, int MODE>
 __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1,
                                            int v0, int v1, const long long (&off)[3],
                                            unsigned ex, unsigned ey, unsigned ez, unsigned *box,
-                                           unsigned cap)
+                                           unsigned cap, const FrameRec *recs)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int u = u0 + kPix * lane;
@@ -115,7 +116,7 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
     const int npx = VEC ? kPix : min(kPix, u1 - u);
     const size_t rstep = (size_t)kWarps * a.W;
     for (int f = f0; f < f1; ++f) {
-        const FrameRec *r = a.rec + f;
+        const FrameRec *r = recs + (f - f0);
         if (!r->valid)
             continue;
         const long long Ax = r->q[0], Ay = r->q[1], Az = r->q[2];
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
 {
     extern __shared__ unsigned box[];
     __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
+    __shared__ FrameRec s_rec[kFpc];
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
@@ -184,14 +186,19 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
     const int u1 = min(a.W, u0 + kTileW), v1 = min(a.H, v0 + a.th);
     const int f0 = blockIdx.y * a.fpc, f1 = min(a.n, f0 + a.fpc);
 
+    // the CTA's frame records, copied once into shared memory
+    for (int i = threadIdx.x; i < (f1 - f0) * (int)(sizeof(FrameRec) / 8); i += kThreads)
+        reinterpret_cast<unsigned long long *>(s_rec)[i] =
+            reinterpret_cast<const unsigned long long *>(a.rec + f0)[i];
+    __syncthreads();
     if (threadIdx.x < 32) {
         // lane i: corner i & 3 of frame f0 + (i >> 2) (up to 8 frames)
         const int lane = threadIdx.x;
         const int f = f0 + (lane >> 2);
         int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
         int cnt = 0, valid = 0;
-        if (f < f1 && a.rec[f].valid) {
-            const FrameRec *r = a.rec + f;
+        if (f < f1 && s_rec[f - f0].valid) {
+            const FrameRec *r = s_rec + (f - f0);
             const long long u = (lane & 1) ? u1 - 1 : u0;
             const long long v = (lane & 2) ? v1 - 1 : v0;
 #pragma unroll
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
         // keys are global linear indices into the whole grid
         const long long off[3] = {1LL << 31, 1LL << 31, 1LL << 31};
         run_frames<VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
-                                           (unsigned)a.ny, (unsigned)a.nz, nullptr, 0);
+                                           (unsigned)a.ny, (unsigned)a.nz, nullptr, 0, s_rec);
         return;
     }
     const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
@@ -264,17 +271,18 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
                               (1LL << 31) - ((long long)s_lo[2] << 32)};
     if (mode == MODE_PACKED) {
         if (s_check)
-            run_frames<VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box, 0);
+            run_frames<VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box, 0,
+                                               s_rec);
         else
             run_frames<VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
-                                                0);
+                                                0, s_rec);
     } else {
         if (s_check)
             run_frames<VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
-                                              cap);
+                                              cap, s_rec);
         else
             run_frames<VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
-                                               cap);
+                                               cap, s_rec);
     }
     __syncthreads();
     // Flush: one warp per box row (fixed y, z), lanes along x.
@@ -318,12 +326,26 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.th = min(32, H);
     a.tiles_x = (W + kTileW - 1) / kTileW;
     const int tiles_y = (H + a.th - 1) / a.th;
-    a.fpc = 4;  // <= 8: warp 0 computes the box from 4 corners x up to 8 frames
+    a.fpc = kFpc;
     const bool vec = (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
     dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
+    // the box plus the CTA's static words exceed the 48 KB default
+    static int attr_device = -1;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn<true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_insert_pnn<false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_device = dev;
+    }
     if (vec)
         k_insert_pnn<true><<<grid, kThreads, kSmem, st>>>(a);
     else
