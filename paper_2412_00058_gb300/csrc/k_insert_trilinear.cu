@@ -11,10 +11,24 @@
 // probe) and walks down its rows, along which the position is affine:
 // q(i) = q(i0) + (i - i0)*d.  The start q(i0) is evaluated in FP64 and split
 // into an integer voxel and a fraction; the fraction and the step d are then
-// carried in Q16.47 fixed point, so after 128 steps the position is still
+// carried in Q16.47 fixed point, so after 16 steps the position is still
 // within ~1e-12 voxel of the FP64 value, and both trilinear factors of an
 // axis, f and 1 - f, are formed from exact integers (no cancellation when f
 // is close to 1).  Columns whose step exceeds 256 voxels re-anchor every row.
+//
+// GB300 design: a CTA takes a tile of 256 columns x 64 rows of 4 consecutive
+// frames; each thread walks one column through the 64 rows, merging the 8
+// corner terms of consecutive samples that stay in one cell (about 1.7
+// samples per 0.4 mm cell along a 0.235 mm-step beam) in registers, and
+// sends each cell's terms to HBM with one vector atomic (S, W) per corner.
+// A conservative voxel box of the tile (FP64 extremes of the patch -- for a
+// convex fan the depth extreme can sit on the central beam -- plus a
+// one-voxel margin) decides whether the tile touches the grid at all and
+// whether its corners need bounds checks; a shared-memory box variant of
+// the accumulation is kept behind kUseBox.
+#include <cfloat>
+#include <climits>
+
 #include "usv_internal.cuh"
 
 namespace usv {
@@ -22,6 +36,17 @@ namespace usv {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kCols = 256;                   // columns per tile
+constexpr int kSegs = kThreads / kCols;      // row segments per tile (1)
+constexpr int kRowsPerSeg = 64;
+constexpr int kRows = kSegs * kRowsPerSeg;   // 64 rows per tile
+constexpr int kFpc = 4;                      // frames per CTA
+constexpr int kBoxBytes = 64 * 1024;
+// Shared FP32 atomic adds measured as a read-retry loop on this part (430
+// instructions per sample, 32 % issue), so the shared box is kept only as
+// an option; tiles send merged cell terms straight to HBM vector atomics.
+constexpr bool kUseBox = false;
+constexpr int kBoxCap = kBoxBytes / 8;       // entries: one S and one W float each
 
 struct TriArgs {
     const void *img;
@@ -33,91 +58,272 @@ struct TriArgs {
     int nx, ny, nz;
     int convex;
     double r0, dr;
-    int th;          // rows per CTA
-    int tiles_x;     // column tiles of kThreads columns
+    int tiles_x;     // column tiles
 };
 
 constexpr long long kOne47 = 1LL << 47;
 constexpr long long kMask47 = kOne47 - 1;
 constexpr float kInv47 = 7.105427357601002e-15f;  // 2^-47
+constexpr float kWmin = 9.5367431640625e-07f;     // 2^-20
 
 // q (FP64, |q| < 2^30) -> integer voxel floor(q) and Q16.47 fraction
 __device__ __forceinline__ void anchor(double q, int &i0, long long &fq)
 {
     const double fl = floor(q);
     i0 = (int)fl;
-    fq = __double2ll_rn((q - fl) * 140737488355328.0);  // (q - floor q) * 2^47, exact split
+    fq = __double2ll_rn((q - fl) * 140737488355328.0);  // (q - floor q) * 2^47
 }
 
-__global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
+// FP64 position (voxel units) of sample (row v, column j) of frame r, and
+// its per-row step.
+__device__ __forceinline__ void sample_line(const TriArgs &a, const FrameRec *r, int j, int v,
+                                            double (&base)[3], double (&step)[3])
 {
-    const int tx = blockIdx.x % a.tiles_x, ty = blockIdx.x / a.tiles_x;
-    const int j = tx * kThreads + threadIdx.x;
-    const int f = blockIdx.y;
-    if (j >= a.W)
-        return;
-    const FrameRec *r = a.rec + f;
-    if (!r->valid)
-        return;
-    const int v0 = ty * a.th, v1 = min(a.H, v0 + a.th);
-
-    // FP64 position of sample (v, j) and its per-row step, per axis
-    double base[3], step[3];
     if (a.convex) {
         const double2 sc = a.beams[j];
+        const double rr = a.r0 + (double)v * a.dr;
         for (int ax = 0; ax < 3; ++ax) {
             const double dA = r->d[ax], dB = r->d[3 + ax], C = r->d[6 + ax];
-            const double rr = a.r0 + (double)v0 * a.dr;
             base[ax] = C + (rr * sc.x) * dA + (rr * sc.y - a.r0) * dB;
             step[ax] = a.dr * (sc.x * dA + sc.y * dB);
         }
     } else {
         for (int ax = 0; ax < 3; ++ax) {
-            base[ax] = r->d[6 + ax] + (double)j * r->d[ax] + (double)v0 * r->d[3 + ax];
+            base[ax] = r->d[6 + ax] + (double)j * r->d[ax] + (double)v * r->d[3 + ax];
             step[ax] = r->d[3 + ax];
         }
     }
-    const bool steep = fabs(step[0]) > 256.0 || fabs(step[1]) > 256.0 || fabs(step[2]) > 256.0;
-    int i0[3];
-    long long fq[3], dq[3];
-    for (int ax = 0; ax < 3; ++ax) {
-        anchor(base[ax], i0[ax], fq[ax]);
-        dq[ax] = __double2ll_rn(step[ax] * 140737488355328.0);
+}
+
+// Conservative voxel range of frame r's samples in columns [j0, j1) x rows
+// [v0, v1): the in-plane (x, z) extremes of the patch, mapped through the
+// affine per-mm (convex) or per-pixel (linear) map.
+__device__ void patch_box(const TriArgs &a, const FrameRec *r, int j0, int j1, int v0, int v1,
+                          double (&lo)[3], double (&hi)[3])
+{
+    double xs[2], zs[2];
+    if (a.convex) {
+        const double ra = a.r0 + (double)v0 * a.dr, rb = a.r0 + (double)(v1 - 1) * a.dr;
+        const double2 sa = a.beams[j0], sb = a.beams[j1 - 1];
+        // x = r sin(theta): monotone in theta, extremes at corners
+        const double x1 = ra * sa.x, x2 = rb * sa.x, x3 = ra * sb.x, x4 = rb * sb.x;
+        xs[0] = fmin(fmin(x1, x2), fmin(x3, x4));
+        xs[1] = fmax(fmax(x1, x2), fmax(x3, x4));
+        // z = r cos(theta) - r0: minimum at a corner, maximum on the central
+        // beam if the patch straddles it
+        const double cmin = fmin(sa.y, sb.y);
+        const double cmax = (sa.x <= 0.0 && sb.x >= 0.0) ? 1.0 : fmax(sa.y, sb.y);
+        zs[0] = ra * cmin - a.r0;
+        zs[1] = rb * cmax - a.r0;
+    } else {
+        xs[0] = (double)j0;  // linear: the map is per pixel, (u, v) directly
+        xs[1] = (double)(j1 - 1);
+        zs[0] = (double)v0;
+        zs[1] = (double)(v1 - 1);
     }
-    const size_t fbase = (size_t)f * a.H * a.W;
-    const float wmin = 9.5367431640625e-07f;  // 2^-20
-    for (int v = v0; v < v1; ++v) {
-        if (steep && v > v0)
-            for (int ax = 0; ax < 3; ++ax)
-                anchor(base[ax] + (double)(v - v0) * step[ax], i0[ax], fq[ax]);
-        const size_t pi = fbase + (size_t)v * a.W + j;
-        const float I = a.is_f32 ? __ldcs(static_cast<const float *>(a.img) + pi)
-                                 : (float)__ldcs(static_cast<const uint8_t *>(a.img) + pi);
-        int ix[3];
-        float w1[3], w0[3];
+    for (int ax = 0; ax < 3; ++ax) {
+        lo[ax] = DBL_MAX;
+        hi[ax] = -DBL_MAX;
+        for (int c = 0; c < 4; ++c) {
+            const double q = r->d[6 + ax] + xs[c & 1] * r->d[ax] + zs[c >> 1] * r->d[3 + ax];
+            lo[ax] = fmin(lo[ax], q);
+            hi[ax] = fmax(hi[ax], q);
+        }
+    }
+}
+
+// Add one sample's 8 corner terms. Box mode: shared arrays, box-local key;
+// direct mode: HBM vector atomics.
+template <bool BOX, bool CHECK>
+__device__ __forceinline__ void splat(float *bS, float *bW, float2 *acc, unsigned ex,
+                                      unsigned ey, unsigned ez, int lx, int ly, int lz,
+                                      const float (&cS)[8], const float (&cW)[8])
+{
 #pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
+        if (cW[c] == 0.0f)
+            continue;
+        const unsigned X = (unsigned)(lx + cx), Y = (unsigned)(ly + cy), Z = (unsigned)(lz + cz);
+        if (CHECK && !(X < ex && Y < ey && Z < ez))
+            continue;
+        if (BOX) {
+            const unsigned k = X + ex * (Y + ey * Z);
+            atomicAdd(bS + k, cS[c]);
+            atomicAdd(bW + k, cW[c]);
+        } else {
+            atomicAdd(acc + ((size_t)Z * ey + Y) * ex + X, make_float2(cS[c], cW[c]));
+        }
+    }
+}
+
+template <bool BOX, bool CHECK>
+__device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int f0, int f1,
+                                     int j, int v0, int v1, const int (&blo)[3], unsigned ex,
+                                     unsigned ey, unsigned ez, float *bS, float *bW)
+{
+    for (int f = f0; f < f1; ++f) {
+        const FrameRec *r = recs + (f - f0);
+        if (!r->valid)
+            continue;
+        double base[3], step[3];
+        sample_line(a, r, j, v0, base, step);
+        const bool steep =
+            fabs(step[0]) > 256.0 || fabs(step[1]) > 256.0 || fabs(step[2]) > 256.0;
+        int i0[3];
+        long long fq[3], dq[3];
         for (int ax = 0; ax < 3; ++ax) {
-            ix[ax] = i0[ax] + (int)(fq[ax] >> 47);
-            const long long fr = fq[ax] & kMask47;
-            w1[ax] = __ll2float_rn(fr) * kInv47;
-            w0[ax] = __ll2float_rn(kOne47 - fr) * kInv47;
+            anchor(base[ax], i0[ax], fq[ax]);
+            dq[ax] = __double2ll_rn(step[ax] * 140737488355328.0);
         }
+        const size_t fbase = (size_t)f * a.H * a.W;
+        // register accumulation of the current cell's 8 corner terms
+        float cS[8], cW[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-            const int X = ix[0] + cx, Y = ix[1] + cy, Z = ix[2] + cz;
-            if ((unsigned)X >= (unsigned)a.nx || (unsigned)Y >= (unsigned)a.ny ||
-                (unsigned)Z >= (unsigned)a.nz)
-                continue;
-            const float w = (cx ? w1[0] : w0[0]) * (cy ? w1[1] : w0[1]) * (cz ? w1[2] : w0[2]);
-            if (w < wmin)
-                continue;
-            atomicAdd(a.acc + ((size_t)Z * a.ny + Y) * a.nx + X, make_float2(w * I, w));
+        for (int c = 0; c < 8; ++c)
+            cS[c] = cW[c] = 0.0f;
+        int cx0 = INT_MIN, cy0 = 0, cz0 = 0;
+        for (int v = v0; v < v1; ++v) {
+            if (steep && v > v0)
+                for (int ax = 0; ax < 3; ++ax)
+                    anchor(base[ax] + (double)(v - v0) * step[ax], i0[ax], fq[ax]);
+            const size_t pi = fbase + (size_t)v * a.W + j;
+            const float I = a.is_f32 ? __ldcs(static_cast<const float *>(a.img) + pi)
+                                     : (float)__ldcs(static_cast<const uint8_t *>(a.img) + pi);
+            int ix[3];
+            float w1[3], w0[3];
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                ix[ax] = i0[ax] + (int)(fq[ax] >> 47) - blo[ax];  // box-local (or global)
+                const long long fr = fq[ax] & kMask47;
+                w1[ax] = __ll2float_rn(fr) * kInv47;
+                w0[ax] = __ll2float_rn(kOne47 - fr) * kInv47;
+            }
+            if (ix[0] != cx0 || ix[1] != cy0 || ix[2] != cz0) {
+                if (cx0 != INT_MIN)
+                    splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    cS[c] = cW[c] = 0.0f;
+                cx0 = ix[0];
+                cy0 = ix[1];
+                cz0 = ix[2];
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float w = ((c & 1) ? w1[0] : w0[0]) * (((c >> 1) & 1) ? w1[1] : w0[1]) *
+                                ((c >> 2) ? w1[2] : w0[2]);
+                if (w >= kWmin) {
+                    cS[c] += w * I;
+                    cW[c] += w;
+                }
+            }
+            if (!steep) {
+                fq[0] += dq[0];
+                fq[1] += dq[1];
+                fq[2] += dq[2];
+            }
         }
-        if (!steep) {
-            fq[0] += dq[0];
-            fq[1] += dq[1];
-            fq[2] += dq[2];
+        if (cx0 != INT_MIN)
+            splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
+{
+    extern __shared__ float tbox[];  // [kBoxCap] S, then [kBoxCap] W
+    __shared__ FrameRec s_rec[kFpc];
+    __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
+    const int tx = blockIdx.x % a.tiles_x, ty = blockIdx.x / a.tiles_x;
+    const int j0 = tx * kCols, j1 = min(a.W, j0 + kCols);
+    const int v0 = ty * kRows, v1 = min(a.H, v0 + kRows);
+    const int f0 = blockIdx.y * kFpc, f1 = min(a.n, f0 + kFpc);
+
+    for (int i = threadIdx.x; i < (f1 - f0) * (int)(sizeof(FrameRec) / 8); i += kThreads)
+        reinterpret_cast<unsigned long long *>(s_rec)[i] =
+            reinterpret_cast<const unsigned long long *>(a.rec + f0)[i];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+        int any = 0;
+        if (lane < f1 - f0 && s_rec[lane].valid) {
+            patch_box(a, s_rec + lane, j0, j1, v0, v1, lo, hi);
+            any = 1;
+        }
+        // reduce over the frames (lanes)
+        for (int off = 16; off > 0; off >>= 1) {
+            any |= __shfl_xor_sync(0xFFFFFFFFu, any, off);
+            for (int ax = 0; ax < 3; ++ax) {
+                lo[ax] = fmin(lo[ax], __shfl_xor_sync(0xFFFFFFFFu, lo[ax], off));
+                hi[ax] = fmax(hi[ax], __shfl_xor_sync(0xFFFFFFFFu, hi[ax], off));
+            }
+        }
+        if (lane == 0) {
+            int mode = 0, check = 0;
+            if (any) {
+                const int n[3] = {a.nx, a.ny, a.nz};
+                long long vol = 1;
+                mode = 1;
+                for (int ax = 0; ax < 3; ++ax) {
+                    // corners reach floor(q) + 1; one voxel of margin each side
+                    const long long l0 = (long long)floor(lo[ax]) - 1;
+                    const long long h0 = (long long)floor(hi[ax]) + 2;
+                    const long long l = l0 < 0 ? 0 : l0, h = h0 > n[ax] - 1 ? n[ax] - 1 : h0;
+                    if (l > h)
+                        mode = 0;
+                    if (l != l0 || h != h0)
+                        check = 1;
+                    s_lo[ax] = (int)l;
+                    s_ext[ax] = (int)(h >= l ? h - l + 1 : 0);
+                    vol *= (h >= l ? h - l + 1 : 0);
+                }
+                if (mode == 1 && (vol > kBoxCap || !kUseBox))
+                    mode = 2;
+            }
+            s_mode = mode;
+            s_check = check;
+        }
+    }
+    __syncthreads();
+    const int mode = s_mode;
+    if (mode == 0)
+        return;
+    const int j = j0 + (threadIdx.x % kCols);
+    const int seg = threadIdx.x / kCols;
+    const int rv0 = v0 + seg * kRowsPerSeg, rv1 = min(v1, rv0 + kRowsPerSeg);
+    float *bS = tbox, *bW = tbox + kBoxCap;
+    if (mode == 2) {
+        const int zero[3] = {0, 0, 0};
+        if (j < j1 && rv0 < rv1)
+            walk<false, true>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
+                              (unsigned)a.ny, (unsigned)a.nz, bS, bW);
+        return;
+    }
+    const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
+    const unsigned bvol = ex * ey * ez;
+    for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
+        bS[i] = 0.0f;
+        bW[i] = 0.0f;
+    }
+    __syncthreads();
+    const int blo[3] = {s_lo[0], s_lo[1], s_lo[2]};
+    if (j < j1 && rv0 < rv1) {
+        if (s_check)
+            walk<true, true>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
+        else
+            walk<true, false>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (unsigned row = warp; row < ey * ez; row += kThreads / 32) {
+        const unsigned ly = row % ey, lz = row / ey;
+        float2 *dst = a.acc + ((size_t)(lz + s_lo[2]) * a.ny + (ly + s_lo[1])) * a.nx + s_lo[0];
+        const size_t o = (size_t)row * ex;
+        for (unsigned lx = lane; lx < ex; lx += 32) {
+            const float w = bW[o + lx];
+            if (w != 0.0f)
+                atomicAdd(dst + lx, make_float2(bS[o + lx], w));
         }
     }
 }
@@ -144,11 +350,23 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     a.convex = convex;
     a.r0 = r0;
     a.dr = dr;
-    a.th = 128;
-    a.tiles_x = (W + kThreads - 1) / kThreads;
-    const int tiles_y = (H + a.th - 1) / a.th;
-    dim3 grid(a.tiles_x * tiles_y, n);
-    k_insert_trilinear<<<grid, kThreads, 0, st>>>(a);
+    a.tiles_x = (W + kCols - 1) / kCols;
+    const int tiles_y = (H + kRows - 1) / kRows;
+    const long long groups = (n + kFpc - 1) / kFpc;
+    if (groups > 65535)
+        return cudaErrorInvalidConfiguration;
+    static int attr_device = -1;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        const cudaError_t e = cudaFuncSetAttribute(
+            k_insert_trilinear, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxBytes);
+        if (e != cudaSuccess)
+            return e;
+        attr_device = dev;
+    }
+    dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
+    k_insert_trilinear<<<grid, kThreads, kBoxBytes, st>>>(a);
     return cudaGetLastError();
 }
 
