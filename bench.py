@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="usvol", choices=["usvol", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--stream-seconds", type=float, default=4.0,
+                   help="seconds of the four-session streaming run (0: skip)")
     p.add_argument("--frames", type=int, default=3600,
                    help="frames of the sweep (fewer = a shorter piece at the same frame "
                         "spacing; for profiling captures)")
@@ -418,6 +420,22 @@ def run_gpu(args):
                "pipeline": f"{len(bounds)} batches of {batch} frames, H2D on a copy stream "
                            "overlapped with insertion"}
 
+    # ---- streaming: four concurrent sessions, frame-to-render latency
+    streaming = None
+    if args.stream_seconds > 0:
+        from paper_2412_00058_gb300 import stream as ustream
+        sched = ustream.Scheduler(dev)
+        for name, sw, fps in synth.streaming_sessions(args.stream_seconds):
+            sched.admit(name, sw, fps, seed=len(sched.sessions))
+        stats = sched.run(args.stream_seconds)
+        streaming = ustream.summary(stats)
+        streaming["seconds"] = args.stream_seconds
+        streaming["what"] = ("per-frame latency from burst arrival on the host to its "
+                             "region-refreshed projection completing on the device; bursts of "
+                             "1-32 frames at 30/60/120/30 fps into 128^3, 256x1024x200, "
+                             "270x1840x200 (PNN) and 400x1700x400 (trilinear) volumes")
+        del sched
+
     # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -448,6 +466,9 @@ def run_gpu(args):
                                   "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
                                   "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak},
             "touched_voxels": touched, "pixel_hits": hits,
+            "p50_frame_to_render_ms": streaming["p50_ms"] if streaming else None,
+            "p99_frame_to_render_ms": streaming["p99_ms"] if streaming else None,
+            "streaming": streaming,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches_per_step * K,
             "clocks": clocks,
         }

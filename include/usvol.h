@@ -158,6 +158,23 @@ int usv_project_depth_band(usv_volume *vol, int32_t z_lo, int32_t z_hi, float *o
                            uint16_t *count_dev, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Region forms, for incremental display (the paper re-processes "only the
+ * areas that need to be updated" after each batch, Sec. II.C):
+ * usv_fill_holes_region refreshes the filled values and mask of the voxels
+ * [lo, hi) (x, y, z; clipped to the grid; x widened down to a multiple of
+ * 32) from the current accumulators -- after inserting frames whose voxels
+ * lie in [a, b), refreshing [a - 1, b + 1) updates everything that changed.
+ * usv_project_depth_band_region recomputes the projection of columns
+ * [xy_lo, xy_hi) only; the rest of out_dev / count_dev is left as it is.
+ * The whole-volume calls are these with the full grid.
+ * ---------------------------------------------------------------------- */
+int usv_fill_holes_region(usv_volume *vol, const int32_t lo[3], const int32_t hi[3],
+                          int32_t radius, void *stream);
+int usv_project_depth_band_region(usv_volume *vol, int32_t z_lo, int32_t z_hi,
+                                  const int32_t xy_lo[2], const int32_t xy_hi[2], float *out_dev,
+                                  uint16_t *count_dev, void *stream);
+
+/* ------------------------------------------------------------------------
  * usv_volume_read -- copy one field to caller device memory in canonical
  * [nz][ny][nx] order (the paper saves the finished volume as slices).
  *   USV_READ_ACCUM : PNN uint64 (low 32 bits sum, high 32 bits count);

@@ -44,6 +44,7 @@ struct FillArgs {
     uint32_t *mask;
     uint32_t *status;
     int nx, ny, nz, nxw, zchunk;
+    int rx0, ry0, rz0, rz1;  // refreshed region: x from rx0 (a multiple of 32), y from ry0, z in [rz0, rz1)
 };
 
 template <typename T>
@@ -112,8 +113,8 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
     __shared__ unsigned sflag[FSLOTS];
     const auto *acc = static_cast<const unsigned long long *>(a.acc);
     auto *val = static_cast<uint8_t *>(a.val);
-    const int x0 = blockIdx.x * FTX, y0 = blockIdx.y * FTY;
-    const int z0 = blockIdx.z * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
+    const int x0 = a.rx0 + blockIdx.x * FTX, y0 = a.ry0 + blockIdx.y * FTY;
+    const int z0 = a.rz0 + blockIdx.z * a.zchunk, z1 = min(a.rz1, z0 + a.zchunk);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
     const int x = x0 + tx, yb = 4 * ty;  // first of this thread's rows (tile-local)
     const size_t plane = (size_t)a.nx * a.ny;
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
     // output pointers of this thread's first row, advanced one plane per output
     const bool xin = x < a.nx;
     uint8_t *vout = val + ((size_t)z0 * a.ny + y0 + yb) * a.nx + x;
-    uint32_t *mout = a.mask + ((size_t)z0 * a.ny + y0 + yb) * a.nxw + blockIdx.x;
+    uint32_t *mout = a.mask + ((size_t)z0 * a.ny + y0 + yb) * a.nxw + (x0 >> 5);
     const size_t mplane = (size_t)a.ny * a.nxw;
     const int nrows = min(FRW, a.ny - (y0 + yb));  // rows of this thread inside the grid
 
@@ -281,8 +282,8 @@ __global__ void __launch_bounds__(TX *TY) k_fill_f32(FillArgs a)
     __shared__ float2 pl[3][PY][PX];
     const auto *acc = static_cast<const float2 *>(a.acc);
     auto *val = static_cast<float *>(a.val);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * a.zchunk, z1 = min(a.nz, z0 + a.zchunk);
+    const int x0 = a.rx0 + blockIdx.x * TX, y0 = a.ry0 + blockIdx.y * TY;
+    const int z0 = a.rz0 + blockIdx.z * a.zchunk, z1 = min(a.rz1, z0 + a.zchunk);
     const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
     const int x = x0 + tx, y = y0 + ty;
     const bool inside = x < a.nx && y < a.ny;
@@ -323,35 +324,38 @@ __global__ void __launch_bounds__(TX *TY) k_fill_f32(FillArgs a)
             val[i] = v;
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, inside && has);
         if (tx == 0 && y < a.ny)
-            a.mask[((size_t)z * a.ny + y) * a.nxw + blockIdx.x] = bits;
+            a.mask[((size_t)z * a.ny + y) * a.nxw + (x0 >> 5)] = bits;
         __syncthreads();
     }
 }
 
-dim3 fill_grid(const Volume &v, int *zchunk)
+// Region [lo, hi) (already clipped to the grid, lo[0] a multiple of 32)
+dim3 fill_grid(FillArgs &a, int tx, int ty, int waves_ctas, const int *lo, const int *hi,
+               int num_sms, int min_slab)
 {
-    const int gx = (v.g.nx + TX - 1) / TX, gy = (v.g.ny + TY - 1) / TY;
-    // enough CTAs for ~8 waves of 8 resident CTAs per SM, slabs >= 16 planes
-    const long long want = (long long)v.num_sms * 8 * 8;
-    long long zc = ((long long)gx * gy * v.g.nz + want - 1) / want;
-    zc = zc < 16 ? 16 : zc;
-    zc = zc > v.g.nz ? v.g.nz : zc;
-    *zchunk = (int)zc;
-    return dim3(gx, gy, (v.g.nz + (int)zc - 1) / (int)zc);
+    const int gx = (hi[0] - lo[0] + tx - 1) / tx, gy = (hi[1] - lo[1] + ty - 1) / ty;
+    const int nzr = hi[2] - lo[2];
+    const long long want = (long long)num_sms * waves_ctas;
+    long long zc = ((long long)gx * gy * nzr + want - 1) / want;
+    zc = zc < min_slab ? min_slab : zc;
+    zc = zc > nzr ? nzr : zc;
+    a.zchunk = (int)(zc < 1 ? 1 : zc);
+    a.rx0 = lo[0];
+    a.ry0 = lo[1];
+    a.rz0 = lo[2];
+    a.rz1 = hi[2];
+    return dim3(gx, gy, (nzr + a.zchunk - 1) / a.zchunk);
 }
 
 }  // namespace
 
-cudaError_t launch_fill_pnn(const Volume &v, cudaStream_t st)
+cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st)
 {
-    FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0};
-    const int gx = (v.g.nx + FTX - 1) / FTX, gy = (v.g.ny + FTY - 1) / FTY;
+    FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0};
     // ~6 waves of 4 resident CTAs per SM; slabs of at least 16 planes
-    const long long want = (long long)v.num_sms * 4 * 6;
-    long long zc = ((long long)gx * gy * v.g.nz + want - 1) / want;
-    zc = zc < 16 ? 16 : zc;
-    zc = zc > v.g.nz ? v.g.nz : zc;
-    a.zchunk = (int)zc;
+    const dim3 grid = fill_grid(a, FTX, FTY, 4 * 6, lo, hi, v.num_sms, 16);
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0)
+        return cudaSuccess;
     static int attr_device = -1;
     int dev = -1;
     cudaGetDevice(&dev);
@@ -362,15 +366,16 @@ cudaError_t launch_fill_pnn(const Volume &v, cudaStream_t st)
             return e;
         attr_device = dev;
     }
-    const dim3 grid(gx, gy, (v.g.nz + a.zchunk - 1) / a.zchunk);
     k_fill_pnn<<<grid, dim3(FTX, FBY), kFillSmem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fill_trilinear(const Volume &v, cudaStream_t st)
+cudaError_t launch_fill_trilinear(const Volume &v, const int *lo, const int *hi, cudaStream_t st)
 {
-    FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0};
-    const dim3 grid = fill_grid(v, &a.zchunk);
+    FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0};
+    const dim3 grid = fill_grid(a, TX, TY, 8 * 8, lo, hi, v.num_sms, 16);
+    if (grid.x == 0 || grid.y == 0 || grid.z == 0)
+        return cudaSuccess;
     k_fill_f32<<<grid, dim3(TX, TY), 0, st>>>(a);
     return cudaGetLastError();
 }

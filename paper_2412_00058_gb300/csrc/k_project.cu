@@ -20,12 +20,13 @@ struct ProjArgs {
     float *out;
     uint16_t *cnt;
     int nx, ny, nxw, lo, hi;
+    int rx0, ry0, rx1, ry1;  // refreshed columns [rx0, rx1) x [ry0, ry1)
 };
 
 __global__ void __launch_bounds__(256) k_project_u8(ProjArgs a)
 {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= a.nx || y >= a.ny)
+    const int x = a.rx0 + blockIdx.x * 32 + threadIdx.x, y = a.ry0 + blockIdx.y * 8 + threadIdx.y;
+    if (x >= a.rx1 || y >= a.ry1)
         return;
     const auto *val = static_cast<const uint8_t *>(a.val);
     const size_t plane = (size_t)a.ny * a.nx, mplane = (size_t)a.ny * a.nxw;
@@ -44,8 +45,8 @@ __global__ void __launch_bounds__(256) k_project_u8(ProjArgs a)
 
 __global__ void __launch_bounds__(256) k_project_f32(ProjArgs a)
 {
-    const int x = blockIdx.x * 32 + threadIdx.x, y = blockIdx.y * 8 + threadIdx.y;
-    if (x >= a.nx || y >= a.ny)
+    const int x = a.rx0 + blockIdx.x * 32 + threadIdx.x, y = a.ry0 + blockIdx.y * 8 + threadIdx.y;
+    if (x >= a.rx1 || y >= a.ry1)
         return;
     const auto *val = static_cast<const float *>(a.val);
     const size_t plane = (size_t)a.ny * a.nx, mplane = (size_t)a.ny * a.nxw;
@@ -66,20 +67,26 @@ __global__ void __launch_bounds__(256) k_project_f32(ProjArgs a)
 
 }  // namespace
 
-cudaError_t launch_project_u8(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
-                              cudaStream_t st)
+cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
+                              float *out, uint16_t *cnt, cudaStream_t st)
 {
-    ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi};
-    dim3 grid((v.g.nx + 31) / 32, (v.g.ny + 7) / 8);
+    ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi,
+               rlo[0], rlo[1], rhi[0], rhi[1]};
+    dim3 grid((rhi[0] - rlo[0] + 31) / 32, (rhi[1] - rlo[1] + 7) / 8);
+    if (grid.x == 0 || grid.y == 0)
+        return cudaSuccess;
     k_project_u8<<<grid, dim3(32, 8), 0, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_project_f32(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
-                               cudaStream_t st)
+cudaError_t launch_project_f32(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
+                               float *out, uint16_t *cnt, cudaStream_t st)
 {
-    ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi};
-    dim3 grid((v.g.nx + 31) / 32, (v.g.ny + 7) / 8);
+    ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi,
+               rlo[0], rlo[1], rhi[0], rhi[1]};
+    dim3 grid((rhi[0] - rlo[0] + 31) / 32, (rhi[1] - rlo[1] + 7) / 8);
+    if (grid.x == 0 || grid.y == 0)
+        return cudaSuccess;
     k_project_f32<<<grid, dim3(32, 8), 0, st>>>(a);
     return cudaGetLastError();
 }

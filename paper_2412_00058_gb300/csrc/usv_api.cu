@@ -269,30 +269,69 @@ int usv_fill_holes(usv_volume *vol, int32_t radius, void *stream)
 {
     if (!vol)
         return USV_ERR_ARG;
+    const Volume &v = *reinterpret_cast<Volume *>(vol);
+    const int32_t lo[3] = {0, 0, 0}, hi[3] = {v.g.nx, v.g.ny, v.g.nz};
+    return usv_fill_holes_region(vol, lo, hi, radius, stream);
+}
+
+int usv_fill_holes_region(usv_volume *vol, const int32_t lo[3], const int32_t hi[3],
+                          int32_t radius, void *stream)
+{
+    if (!vol || !lo || !hi)
+        return USV_ERR_ARG;
     if (radius != 1)
         return USV_ERR_UNSUPPORTED;
     Volume &v = *reinterpret_cast<Volume *>(vol);
+    const int n[3] = {v.g.nx, v.g.ny, v.g.nz};
+    int l[3], h[3];
+    for (int a = 0; a < 3; ++a) {
+        l[a] = lo[a] < 0 ? 0 : lo[a];
+        h[a] = hi[a] > n[a] ? n[a] : hi[a];
+        if (l[a] >= h[a])
+            return USV_OK;  // empty region
+    }
+    l[0] &= ~31;  // mask words cover 32 columns
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    return usv::cuda_rc(v.mode == USV_PNN ? usv::launch_fill_pnn(v, st)
-                                          : usv::launch_fill_trilinear(v, st));
+    return usv::cuda_rc(v.mode == USV_PNN ? usv::launch_fill_pnn(v, l, h, st)
+                                          : usv::launch_fill_trilinear(v, l, h, st));
 }
 
 int usv_project_depth_band(usv_volume *vol, int32_t z_lo, int32_t z_hi, float *out_dev,
                            uint16_t *count_dev, void *stream)
 {
-    if (!vol || !out_dev)
+    if (!vol)
+        return USV_ERR_ARG;
+    const Volume &v = *reinterpret_cast<Volume *>(vol);
+    const int32_t lo[2] = {0, 0}, hi[2] = {v.g.nx, v.g.ny};
+    return usv_project_depth_band_region(vol, z_lo, z_hi, lo, hi, out_dev, count_dev, stream);
+}
+
+int usv_project_depth_band_region(usv_volume *vol, int32_t z_lo, int32_t z_hi,
+                                  const int32_t xy_lo[2], const int32_t xy_hi[2], float *out_dev,
+                                  uint16_t *count_dev, void *stream)
+{
+    if (!vol || !out_dev || !xy_lo || !xy_hi)
         return USV_ERR_ARG;
     Volume &v = *reinterpret_cast<Volume *>(vol);
     if (z_lo < 0 || z_hi > v.g.nz || z_lo >= z_hi)
         return USV_ERR_RANGE;
     if (z_hi - z_lo > 65535)
         return USV_ERR_RANGE;
+    const int n[2] = {v.g.nx, v.g.ny};
+    int l[2], h[2];
+    for (int a = 0; a < 2; ++a) {
+        l[a] = xy_lo[a] < 0 ? 0 : xy_lo[a];
+        h[a] = xy_hi[a] > n[a] ? n[a] : xy_hi[a];
+        if (l[a] >= h[a])
+            return USV_OK;
+    }
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     return usv::cuda_rc(v.mode == USV_PNN
-                            ? usv::launch_project_u8(v, z_lo, z_hi, out_dev, count_dev, st)
-                            : usv::launch_project_f32(v, z_lo, z_hi, out_dev, count_dev, st));
+                            ? usv::launch_project_u8(v, z_lo, z_hi, l, h, out_dev, count_dev, st)
+                            : usv::launch_project_f32(v, z_lo, z_hi, l, h, out_dev, count_dev,
+                                                      st));
 }
 
 int usv_volume_read(usv_volume *vol, int32_t what, void *dst_dev, void *stream)

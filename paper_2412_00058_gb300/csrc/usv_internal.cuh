@@ -64,12 +64,14 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
                               cudaStream_t st);
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
                                     int W, int convex, double r0, double dr, cudaStream_t st);
-cudaError_t launch_fill_pnn(const Volume &v, cudaStream_t st);
-cudaError_t launch_fill_trilinear(const Volume &v, cudaStream_t st);
-cudaError_t launch_project_u8(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
-                              cudaStream_t st);
-cudaError_t launch_project_f32(const Volume &v, int lo, int hi, float *out, uint16_t *cnt,
-                               cudaStream_t st);
+// fill / project a region: voxels [lo, hi) (clipped to the grid; the fill
+// needs lo[0] a multiple of 32), columns [rlo, rhi)
+cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st);
+cudaError_t launch_fill_trilinear(const Volume &v, const int *lo, const int *hi, cudaStream_t st);
+cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
+                              float *out, uint16_t *cnt, cudaStream_t st);
+cudaError_t launch_project_f32(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
+                               float *out, uint16_t *cnt, cudaStream_t st);
 cudaError_t launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t st);
 cudaError_t launch_unpack_mask(const Volume &v, uint8_t *dst, cudaStream_t st);
 

@@ -295,3 +295,29 @@ def pose_refine(seed: int = SEED_BASE + 4, n: int = 512, H: int = 256, W: int = 
     return Workload("pose_refine", imgs, poses, calib, tuple(grid), (spacing,) * 3,
                     (0.0, 0.0, 0.0), tuple(band), mode="trilinear", sx=px, sy=px,
                     meta=dict(seed=seed, noisy_poses=noisy))
+
+
+# ----------------------------------------------------------------------------
+# workload 4: concurrent streaming sessions
+# ----------------------------------------------------------------------------
+
+def streaming_sessions(seconds: float = 4.0, seed: int = SEED_BASE + 3):
+    """Four concurrent scans (name, workload, frames per second): a 128^3
+    volume at 30 fps, a 256 x 1024 x 200 spine piece at 60 fps, the whole
+    spine 270 x 1840 x 200 at 120 fps and the 400 x 1700 x 400 convex fan
+    (trilinear) at 30 fps, each with enough frames for `seconds` of scan."""
+    out = []
+    n1 = max(2, int(30 * seconds) + 1)
+    out.append(("tiny_128", tiny_pnn(seed=seed, n=n1, sweep_mm=20.0), 30.0))
+    n2 = max(2, int(60 * seconds) + 1)
+    out.append(("spine_256x1024x200",
+                whole_spine(seed=seed + 1, n=n2, grid=(256, 1024, 200),
+                            y_start_mm=10.0, y_span_mm=min(280.0, n2 * 550.0 / 3599.0)), 60.0))
+    n3 = max(2, int(120 * seconds) + 1)
+    out.append(("spine_270x1840x200",
+                whole_spine(seed=seed + 2, n=n3, y_span_mm=min(550.0, n3 * 550.0 / 3599.0)),
+                120.0))
+    n4 = max(2, int(30 * seconds) + 1)
+    out.append(("convex_400x1700x400",
+                convex_fan(seed=seed + 3, n=n4, sweep_mm=min(660.0, n4 * 660.0 / 2999.0)), 30.0))
+    return out

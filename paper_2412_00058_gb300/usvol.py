@@ -33,7 +33,8 @@ READ_ACCUM, READ_VALUES, READ_MASK = 0, 1, 2
 EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_volume_reset",
            "usv_insert_frames", "usv_fill_holes", "usv_project_depth_band", "usv_volume_read",
            "usv_volume_write_accum", "usv_status", "usv_strerror", "usv_last_cuda_error",
-           "usv_abi_version", "usv_insert_pnn_noalloc")
+           "usv_abi_version", "usv_insert_pnn_noalloc", "usv_fill_holes_region",
+           "usv_project_depth_band_region")
 
 
 class UsvError(RuntimeError):
@@ -85,6 +86,11 @@ def lib():
             L.usv_fill_holes.restype = ctypes.c_int
             L.usv_project_depth_band.argtypes = [P, I, I, P, P, P]
             L.usv_project_depth_band.restype = ctypes.c_int
+            I3 = ctypes.POINTER(ctypes.c_int32)
+            L.usv_fill_holes_region.argtypes = [P, I3, I3, I, P]
+            L.usv_fill_holes_region.restype = ctypes.c_int
+            L.usv_project_depth_band_region.argtypes = [P, I, I, I3, I3, P, P, P]
+            L.usv_project_depth_band_region.restype = ctypes.c_int
             L.usv_volume_read.argtypes = [P, I, P, P]
             L.usv_volume_read.restype = ctypes.c_int
             L.usv_volume_write_accum.argtypes = [P, P, P]
@@ -173,6 +179,25 @@ def project_depth_band(handle: int, z_lo: int, z_hi: int, out_ptr: int, count_pt
                                         ctypes.c_void_p(out_ptr), ctypes.c_void_p(count_ptr or 0),
                                         ctypes.c_void_p(_stream_ptr(stream))),
            "usv_project_depth_band")
+
+
+def _i32(v) -> ctypes.Array:
+    return (ctypes.c_int32 * len(v))(*[int(x) for x in v])
+
+
+def fill_holes_region(handle: int, lo, hi, radius: int = 1, stream=None) -> None:
+    _check(lib().usv_fill_holes_region(ctypes.c_void_p(handle), _i32(lo), _i32(hi), radius,
+                                       ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_fill_holes_region")
+
+
+def project_depth_band_region(handle: int, z_lo: int, z_hi: int, xy_lo, xy_hi, out_ptr: int,
+                              count_ptr: int | None, stream=None) -> None:
+    _check(lib().usv_project_depth_band_region(ctypes.c_void_p(handle), z_lo, z_hi, _i32(xy_lo),
+                                               _i32(xy_hi), ctypes.c_void_p(out_ptr),
+                                               ctypes.c_void_p(count_ptr or 0),
+                                               ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_project_depth_band_region")
 
 
 def volume_read(handle: int, what: int, dst_ptr: int, stream=None) -> None:

@@ -62,3 +62,45 @@ def test_trilinear_bad_pose_skipped():
     g, o = gpu_run(w), oracle_run(w)
     assert o["skipped"] == 1 and g["status"] & usvol.STATUS_BAD_POSE
     assert_trilinear_close(g, o)
+
+
+@pytest.mark.slow
+def test_convex_fan_full_size_slab_against_oracle():
+    """Full-size convex sweep (3000 frames of 512x512 into 400x1700x400) in
+    the launch configuration of the timed path; the oracle recomputes one
+    y-slab of 12 voxel rows from the frames that can reach it (a frame's
+    y-extent is exact from the 4 corners of its in-plane bounding box, the
+    map being affine) and the GPU's S, W and filled values in the slab's
+    interior rows must match."""
+    import math
+    import oracle
+    from paper_2412_00058_gb300 import synth
+    from helpers import close
+    w = synth.convex_fan()
+    g = gpu_run(w)
+    y0, y1 = 800, 812
+    half = math.radians(w.sector_deg) / 2
+    R = w.r0 + (w.H - 1) * w.dr
+    xs = (-R * math.sin(half), R * math.sin(half))
+    zs = (w.r0 * math.cos(half) - w.r0, R - w.r0)
+    keep = []
+    for f in range(w.n):
+        ys = [(w.poses[f] @ w.calib @ np.array([x, 0.0, z, 1.0]))[1] for x in xs for z in zs]
+        qy0 = (min(ys) - w.origin[1]) / w.spacing[1]
+        qy1 = (max(ys) - w.origin[1]) / w.spacing[1]
+        if qy1 >= y0 - 2 and qy0 <= y1 + 1:
+            keep.append(f)
+    assert 10 < len(keep) < w.n
+    S, Wt, sk = oracle.insert_trilinear(w.grid, w.images[keep], w.poses[keep], w.calibration(),
+                                        w.spacing, w.origin)
+    assert sk == 0
+    val, has = oracle.fill_trilinear(S, Wt)
+    inner = slice(y0 + 1, y1 - 1)       # the fill reads one row beyond each side
+    m = Wt[:, inner, :] >= 2.0 ** -18
+    for k, o in (("S", S), ("W", Wt)):
+        ok, worst = close(g[k][:, inner, :], o[:, inner, :], mask=m)
+        assert ok, f"{k}: worst error / tolerance = {worst:.3g}"
+    both = (g["has"][:, inner, :] == 1) & (has[:, inner, :] == 1) & m
+    ok, worst = close(g["val"][:, inner, :], val[:, inner, :], mask=both)
+    assert ok, f"values: worst error / tolerance = {worst:.3g}"
+    assert m.sum() > 100_000
