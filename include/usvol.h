@@ -134,6 +134,62 @@ int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_
                       void *stream);
 
 /* ------------------------------------------------------------------------
+ * Tissue segmentation by depth of cut (the paper's Algorithms 1 and 2,
+ * Sec. II.D): rows of a frame above its "depth of cut" -- the superficial
+ * tissue over the bone -- are not inserted (Alg. 1 step 5, Alg. 2 step 4).
+ *
+ * usv_insert_frames_cut -- usv_insert_frames with first_row_dev[n] (device
+ *   int32): rows v < first_row_dev[f] of frame f are cut away (for a convex
+ *   probe: radial samples i < first_row).  Negative values keep every row.
+ *
+ * usv_cut_rows_alg1 -- Alg. 1 (real-time): first_row_dev[f] = the row of
+ *   depth Cut_f = K * |P_c1.x - P_cf.x - L/2| + D (Alg. 1 step 4).  P_cf is
+ *   the world position of frame f's upper-left pixel, pose * calibration *
+ *   (0,0,0,1); ".x" is the coordinate along spine_dir (the paper's x axis,
+ *   the spine direction, given in world coordinates); P_c1 (p1_mm) is that
+ *   of the scan's first frame (the neck), kept by the caller across
+ *   batches.  Computed in FP64, each operation rounded in order:
+ *   d = ((p1x-px)*ex + (p1y-py)*ey) + (p1z-pz)*ez; cut = K*|d - L/2| + D;
+ *   row = ceil(cut / row_mm) clamped to [0, H], row_mm = sy_mm (linear) or
+ *   dr_mm (convex).  K, D, L are the paper's user constants.
+ *
+ * usv_bone_rows_alg2 -- Alg. 2 (after the scan, uint8 frames): in rows
+ *   v >= search_from_row (the lower image, step 2) the score
+ *   I(v,u) * max(0, I(v,u) - I(v+drop_rows,u)) marks a bright contour with
+ *   a shadow below it; per column the first row of the maximum score
+ *   (search_from_row if all are 0), per frame the lower median over the
+ *   columns -> bone_row_dev[f]; then the lower median over the frames
+ *   [f - window/2, f + window/2] clipped to the scan (step 3, window odd)
+ *   minus margin_rows, at least 0 -> first_row_dev[f].  Exact integers.
+ *   H <= USV_ALG2_MAX_ROWS.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    double K;            /* cut depth per distance from the middle of the back (mm/mm) */
+    double D_mm;         /* cut depth at the middle of the back (mm) */
+    double L_mm;         /* length of the back (mm) */
+    double spine_dir[3]; /* unit vector along the spine (the paper's x), world coordinates */
+    double p1_mm[3];     /* world position of the first frame's upper-left pixel (mm) */
+} usv_alg1_params;
+
+typedef struct {
+    int32_t search_from_row; /* first row searched for the bone contour */
+    int32_t drop_rows;       /* the shadow is compared this many rows below (>= 1) */
+    int32_t window;          /* temporal median window in frames (odd, >= 1) */
+    int32_t margin_rows;     /* rows kept above the median bone row (>= 0) */
+} usv_alg2_params;
+
+#define USV_ALG2_MAX_ROWS 8192
+
+int usv_insert_frames_cut(usv_volume *vol, const void *images_dev, int32_t n, int32_t H,
+                          int32_t W, int32_t dtype, const double *poses_dev,
+                          const usv_calibration *cal, const int32_t *first_row_dev, void *stream);
+int usv_cut_rows_alg1(const double *poses_dev, int32_t n, int32_t H, const usv_calibration *cal,
+                      const usv_alg1_params *p, int32_t *first_row_dev, void *stream);
+int usv_bone_rows_alg2(const uint8_t *images_dev, int32_t n, int32_t H, int32_t W,
+                       const usv_alg2_params *p, int32_t *bone_row_dev, int32_t *first_row_dev,
+                       void *stream);
+
+/* ------------------------------------------------------------------------
  * usv_fill_holes -- normalisation + hole filling (PNN's second stage; the
  * 3x3x3 neighbourhood is radius 1, the only radius built).  One pass that
  * reads only the accumulators, so it can be re-run after more inserts:

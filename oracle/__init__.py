@@ -77,6 +77,15 @@ def _load():
             lib.ora_fill_trilinear.restype = None
             lib.ora_project_f64.argtypes = [P, P, I, I, I, I, I, P, P]
             lib.ora_project_f64.restype = None
+            lib.ora_insert_pnn_rows.argtypes = [P, P, I, I, I, P, I, I, I, P, P, D, D, P, P, P]
+            lib.ora_insert_pnn_rows.restype = ctypes.c_int64
+            lib.ora_insert_trilinear_rows.argtypes = [P, P, I, I, I, P, I, I, I, I, P, P,
+                                                      ctypes.POINTER(_Geometry), P, P, P]
+            lib.ora_insert_trilinear_rows.restype = ctypes.c_int64
+            lib.ora_cut_rows_alg1.argtypes = [P, I, I, P, D, D, D, P, P, D, P, P]
+            lib.ora_cut_rows_alg1.restype = None
+            lib.ora_bone_rows_alg2.argtypes = [P, I, I, I, I, I, I, I, P, P]
+            lib.ora_bone_rows_alg2.restype = None
             _lib = lib
     return _lib
 
@@ -106,9 +115,11 @@ def frame_affine_q32(pose, calib, sx, sy, spacing, origin):
     return out, bool(ok)
 
 
-def insert_pnn(grid, images, poses, calib, sx, sy, spacing, origin, sum_=None, cnt=None):
+def insert_pnn(grid, images, poses, calib, sx, sy, spacing, origin, sum_=None, cnt=None,
+               first_rows=None):
     """Nearest-neighbour insertion; returns (sum u64[nz,ny,nx], cnt u32[...],
-    frames skipped).  Pass sum_/cnt to continue an existing scan."""
+    frames skipped).  Pass sum_/cnt to continue an existing scan;
+    first_rows[f] cuts away the rows above it (depth of cut)."""
     nx, ny, nz = (int(g) for g in grid)
     images = np.ascontiguousarray(images, dtype=np.uint8)
     n, H, W = images.shape
@@ -116,9 +127,11 @@ def insert_pnn(grid, images, poses, calib, sx, sy, spacing, origin, sum_=None, c
         sum_ = np.zeros((nz, ny, nx), dtype=np.uint64)
         cnt = np.zeros((nz, ny, nx), dtype=np.uint32)
     poses = _f64(poses, (n, 16))
-    sk = _load().ora_insert_pnn(_ptr(sum_), _ptr(cnt), nx, ny, nz, _ptr(images), n, H, W,
-                                _ptr(poses), _ptr(_f64(calib, 16)), float(sx), float(sy),
-                                _ptr(_f64(spacing, 3)), _ptr(_f64(origin, 3)))
+    fr = None if first_rows is None else np.ascontiguousarray(first_rows, dtype=np.int32)
+    sk = _load().ora_insert_pnn_rows(_ptr(sum_), _ptr(cnt), nx, ny, nz, _ptr(images), n, H, W,
+                                     _ptr(poses), _ptr(_f64(calib, 16)), float(sx), float(sy),
+                                     _ptr(_f64(spacing, 3)), _ptr(_f64(origin, 3)),
+                                     _ptr(fr) if fr is not None else None)
     return sum_, cnt, int(sk)
 
 
@@ -148,7 +161,8 @@ def _geometry(cal: dict) -> _Geometry:
                      float(cal.get("sector_deg", 0.0)))
 
 
-def insert_trilinear(grid, images, poses, cal: dict, spacing, origin, S=None, Wt=None):
+def insert_trilinear(grid, images, poses, cal: dict, spacing, origin, S=None, Wt=None,
+                     first_rows=None):
     """Trilinear splat in FP64; returns (S, Wt, frames skipped).  ``cal`` is
     the dict of Workload.calibration()."""
     nx, ny, nz = (int(g) for g in grid)
@@ -161,10 +175,14 @@ def insert_trilinear(grid, images, poses, cal: dict, spacing, origin, S=None, Wt
         S = np.zeros((nz, ny, nx), dtype=np.float64)
         Wt = np.zeros((nz, ny, nx), dtype=np.float64)
     g = _geometry(cal)
-    sk = _load().ora_insert_trilinear(_ptr(S), _ptr(Wt), nx, ny, nz, _ptr(images),
-                                      1 if is_f32 else 0, n, H, W, _ptr(_f64(poses, (n, 16))),
-                                      _ptr(_f64(cal["image_to_probe"], 16)), ctypes.byref(g),
-                                      _ptr(_f64(spacing, 3)), _ptr(_f64(origin, 3)))
+    fr = None if first_rows is None else np.ascontiguousarray(first_rows, dtype=np.int32)
+    sk = _load().ora_insert_trilinear_rows(_ptr(S), _ptr(Wt), nx, ny, nz, _ptr(images),
+                                           1 if is_f32 else 0, n, H, W,
+                                           _ptr(_f64(poses, (n, 16))),
+                                           _ptr(_f64(cal["image_to_probe"], 16)),
+                                           ctypes.byref(g), _ptr(_f64(spacing, 3)),
+                                           _ptr(_f64(origin, 3)),
+                                           _ptr(fr) if fr is not None else None)
     return S, Wt, int(sk)
 
 
@@ -183,3 +201,26 @@ def project_f64(val, has, lo, hi):
     _load().ora_project_f64(_ptr(val), _ptr(has), nx, ny, nz, int(lo), int(hi), _ptr(out),
                             _ptr(c))
     return out, c
+
+
+def cut_rows_alg1(poses, H, calib, k, d_mm, l_mm, spine_dir, p1, row_mm):
+    """Algorithm 1 depth of cut: (first rows int32[n], cut depth mm f64[n])."""
+    poses = np.asarray(poses, np.float64)
+    n = poses.shape[0]
+    rows = np.empty(n, np.int32)
+    cut = np.empty(n, np.float64)
+    _load().ora_cut_rows_alg1(_ptr(_f64(poses, (n, 16))), n, int(H), _ptr(_f64(calib, 16)),
+                              float(k), float(d_mm), float(l_mm), _ptr(_f64(spine_dir, 3)),
+                              _ptr(_f64(p1, 3)), float(row_mm), _ptr(rows), _ptr(cut))
+    return rows, cut
+
+
+def bone_rows_alg2(images, from_row, drop, window, margin):
+    """Algorithm 2: (per-frame bone row int32[n], first rows int32[n])."""
+    images = np.ascontiguousarray(images, dtype=np.uint8)
+    n, H, W = images.shape
+    bone = np.empty(n, np.int32)
+    rows = np.empty(n, np.int32)
+    _load().ora_bone_rows_alg2(_ptr(images), n, H, W, int(from_row), int(drop), int(window),
+                               int(margin), _ptr(bone), _ptr(rows))
+    return bone, rows

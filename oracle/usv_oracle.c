@@ -24,6 +24,12 @@
  *   ora_insert_trilinear   distance-weighted (trilinear) splatting variant,
  *   ora_fill_trilinear     its normalisation + hole fill, and
  *   ora_project_f64        its depth-band projection, all in FP64.
+ *   ora_cut_rows_alg1      Algorithm 1 (real-time depth of cut from the
+ *                          probe position along the spine, Table I).
+ *   ora_bone_rows_alg2     Algorithm 2 (depth of cut from the bone contour
+ *                          and a median filter over frames, Table II).
+ *   ora_insert_pnn_rows    PNN insertion of the rows below each frame's
+ *   ora_insert_trilinear_rows  depth of cut (Alg. 1 step 5-6, Alg. 2 4-5).
  *
  * Where the paper is silent the reading taken is stated at the function.
  * Build with -ffp-contract=off: the affine set-up is defined as separately
@@ -126,6 +132,18 @@ int64_t ora_insert_pnn(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz,
                        const double K[16], double sx, double sy,
                        const double spacing[3], const double origin[3])
 {
+    return ora_insert_pnn_rows(sum, cnt, nx, ny, nz, images, n, H, W, poses, K, sx, sy, spacing,
+                               origin, 0);
+}
+
+/* As ora_insert_pnn, inserting only rows v >= first_rows[f] of frame f
+ * (all rows if first_rows is NULL): the image below the depth of cut. */
+int64_t ora_insert_pnn_rows(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz,
+                            const uint8_t *images, int n, int H, int W, const double *poses,
+                            const double K[16], double sx, double sy,
+                            const double spacing[3], const double origin[3],
+                            const int32_t *first_rows)
+{
     int64_t skipped = 0;
     const int64_t half = (int64_t)1 << 31;
     const int64_t one = (int64_t)1 << 32;
@@ -136,7 +154,8 @@ int64_t ora_insert_pnn(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz,
             continue;
         }
         const uint8_t *img = images + (size_t)f * H * W;
-        for (int v = 0; v < H; ++v)
+        const int v_first = first_rows ? (first_rows[f] > 0 ? first_rows[f] : 0) : 0;
+        for (int v = v_first; v < H; ++v)
             for (int u = 0; u < W; ++u) {
                 int64_t idx[3];
                 for (int a = 0; a < 3; ++a) {
@@ -279,6 +298,17 @@ int64_t ora_insert_trilinear(double *S, double *Wt, int nx, int ny, int nz,
                              const double *poses, const double K[16], const ora_geometry *g,
                              const double spacing[3], const double origin[3])
 {
+    return ora_insert_trilinear_rows(S, Wt, nx, ny, nz, images, is_f32, n, H, W, poses, K, g,
+                                     spacing, origin, 0);
+}
+
+/* As ora_insert_trilinear, skipping rows i < first_rows[f] of frame f. */
+int64_t ora_insert_trilinear_rows(double *S, double *Wt, int nx, int ny, int nz,
+                                  const void *images, int is_f32, int n, int H, int W,
+                                  const double *poses, const double K[16],
+                                  const ora_geometry *g, const double spacing[3],
+                                  const double origin[3], const int32_t *first_rows)
+{
     int64_t skipped = 0;
     const double wmin = 1.0 / 1048576.0; /* 2^-20 */
     for (int f = 0; f < n; ++f) {
@@ -299,7 +329,8 @@ int64_t ora_insert_trilinear(double *S, double *Wt, int nx, int ny, int nz,
             ++skipped;
             continue;
         }
-        for (int i = 0; i < H; ++i)
+        const int i_first = first_rows ? (first_rows[f] > 0 ? first_rows[f] : 0) : 0;
+        for (int i = i_first; i < H; ++i)
             for (int j = 0; j < W; ++j) {
                 double xi, zi, q[3], fr[3];
                 int64_t i0[3];
@@ -395,4 +426,92 @@ void ora_project_f64(const double *val, const uint8_t *has, int nx, int ny, int 
             if (cnt)
                 cnt[(size_t)y * nx + x] = (uint16_t)c;
         }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Tissue segmentation: depth of cut (Algorithms 1 and 2).                    */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Algorithm 1 (Table I): Cut_n = K |P_c1.x - P_cn.x - L/2| + D, where P_cn
+ * is the position of frame n's upper-left pixel (step 3) and .x the
+ * coordinate along the spine (step 4).  Reading: P_cn = pose * calib *
+ * (0,0,0,1), ".x" = dot with the unit spine direction e, P_c1 = p1 (the
+ * scan's first frame); the first row kept is ceil(Cut_n / row_mm), clamped
+ * to [0, H].  FP64, operations in this order, no fused multiply-add.
+ */
+void ora_cut_rows_alg1(const double *poses, int n, int H, const double K[16], double k,
+                       double d_mm, double l_mm, const double e[3], const double p1[3],
+                       double row_mm, int32_t *rows, double *cut_mm)
+{
+    for (int f = 0; f < n; ++f) {
+        const double *P = poses + (size_t)f * 16;
+        double M[3][4], pos[3];
+        pose_times_calib(P, K, M);
+        for (int a = 0; a < 3; ++a)
+            pos[a] = M[a][3];
+        double d = (p1[0] - pos[0]) * e[0];
+        d = d + (p1[1] - pos[1]) * e[1];
+        d = d + (p1[2] - pos[2]) * e[2];
+        const double cut = k * fabs(d - l_mm * 0.5) + d_mm;
+        const double row = ceil(cut / row_mm);
+        int r = 0;
+        if (row > 0.0)
+            r = row >= (double)H ? H : (int)row;
+        rows[f] = r;
+        if (cut_mm)
+            cut_mm[f] = cut;
+    }
+}
+
+static int cmp_i32(const void *a, const void *b)
+{
+    const int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+/*
+ * Algorithm 2 (Table II).  Step 2 -- contours at the bottom of the image
+ * with a large gradient and a high value: in rows v >= from, score(v, u) =
+ * I(v,u) * max(0, I(v,u) - I(v+drop,u)) (a bright cortex over its acoustic
+ * shadow); the column's contour row is the first v of the maximum score
+ * (from if all scores are 0); the frame's bone row is the lower median over
+ * its columns.  Step 3 -- median filtering over all frames: the lower
+ * median of the bone rows in [n - window/2, n + window/2] clipped to the
+ * scan.  The depth of cut keeps `margin` rows above it (at least row 0).
+ */
+void ora_bone_rows_alg2(const uint8_t *images, int n, int H, int W, int from, int drop,
+                        int window, int margin, int32_t *bone, int32_t *rows)
+{
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(W > window ? W : window));
+    for (int f = 0; f < n; ++f) {
+        const uint8_t *img = images + (size_t)f * H * W;
+        for (int u = 0; u < W; ++u) {
+            long best = -1;
+            int brow = from;
+            for (int v = from; v + drop < H; ++v) {
+                const int a = img[(size_t)v * W + u];
+                const int b = img[(size_t)(v + drop) * W + u];
+                const long s = (long)a * (a > b ? a - b : 0);
+                if (s > best) {
+                    best = s;
+                    brow = v;
+                }
+            }
+            col[u] = best > 0 ? brow : from;
+        }
+        qsort(col, (size_t)W, sizeof(int32_t), cmp_i32);
+        bone[f] = col[(W - 1) / 2];
+    }
+    for (int f = 0; f < n; ++f) {
+        const int k0 = f - window / 2 < 0 ? 0 : f - window / 2;
+        const int k1 = f + window / 2 > n - 1 ? n - 1 : f + window / 2;
+        const int len = k1 - k0 + 1;
+        for (int k = 0; k < len; ++k)
+            col[k] = bone[k0 + k];
+        qsort(col, (size_t)len, sizeof(int32_t), cmp_i32);
+        const int med = col[(len - 1) / 2];
+        rows[f] = med - margin > 0 ? med - margin : 0;
+    }
+    free(col);
 }

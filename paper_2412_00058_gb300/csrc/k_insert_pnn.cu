@@ -151,6 +151,14 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
             uint2 wn = make_uint2(0u, 0u);
             if (more)
                 wn = load(src + rstep);
+            if (v < r->first_row) {  // cut away (tissue segmentation)
+                qx += Rx;
+                qy += Ry;
+                qz += Rz;
+                src += rstep;
+                w = wn;
+                continue;
+            }
             bool inside = true;
             if (CHECK) {
                 const long long lx = qx + Ex, ly = qy + Ey, lz = qz + Ez;

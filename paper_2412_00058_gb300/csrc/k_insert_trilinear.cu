@@ -166,8 +166,11 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
         const FrameRec *r = recs + (f - f0);
         if (!r->valid)
             continue;
+        const int vs = max(v0, r->first_row);  // rows above the cut are not inserted
+        if (vs >= v1)
+            continue;
         double base[3], step[3];
-        sample_line(a, r, j, v0, base, step);
+        sample_line(a, r, j, vs, base, step);
         const bool steep =
             fabs(step[0]) > 256.0 || fabs(step[1]) > 256.0 || fabs(step[2]) > 256.0;
         int i0[3];
@@ -183,10 +186,10 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
         for (int c = 0; c < 8; ++c)
             cS[c] = cW[c] = 0.0f;
         int cx0 = INT_MIN, cy0 = 0, cz0 = 0;
-        for (int v = v0; v < v1; ++v) {
-            if (steep && v > v0)
+        for (int v = vs; v < v1; ++v) {
+            if (steep && v > vs)
                 for (int ax = 0; ax < 3; ++ax)
-                    anchor(base[ax] + (double)(v - v0) * step[ax], i0[ax], fq[ax]);
+                    anchor(base[ax] + (double)(v - vs) * step[ax], i0[ax], fq[ax]);
             const size_t pi = fbase + (size_t)v * a.W + j;
             const float I = a.is_f32 ? __ldcs(static_cast<const float *>(a.img) + pi)
                                      : (float)__ldcs(static_cast<const uint8_t *>(a.img) + pi);

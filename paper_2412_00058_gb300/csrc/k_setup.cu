@@ -97,7 +97,8 @@ __global__ void k_frame_setup(const double *__restrict__ poses, int n, SetupPara
         r.q[i] = ok ? q32_round(r.d[i]) : 0;
     r.valid = ok ? 1 : 0;
     r.nmax = ok ? pixels_per_voxel_bound(r.d) : (1 << 20);
-    r.pad[0] = r.pad[1] = 0;
+    r.first_row = sp.first_rows ? max(sp.first_rows[f], 0) : 0;
+    r.pad = 0;
     rec[f] = r;
     if (!ok)
         atomicOr(status, USV_STATUS_BAD_POSE);

@@ -191,9 +191,86 @@ int usv_volume_reset(usv_volume *vol, void *stream)
     return usv::cuda_rc(e);
 }
 
+namespace usv {
+int insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                const int32_t *first_rows_dev, void *stream);
+}
+
 int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                       int32_t dtype, const double *poses_dev, const usv_calibration *cal,
                       void *stream)
+{
+    return usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream);
+}
+
+int usv_insert_frames_cut(usv_volume *vol, const void *images_dev, int32_t n, int32_t H,
+                          int32_t W, int32_t dtype, const double *poses_dev,
+                          const usv_calibration *cal, const int32_t *first_row_dev, void *stream)
+{
+    if (!first_row_dev && n > 0)
+        return USV_ERR_ARG;
+    return usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, first_row_dev,
+                            stream);
+}
+
+int usv_cut_rows_alg1(const double *poses_dev, int32_t n, int32_t H, const usv_calibration *cal,
+                      const usv_alg1_params *p, int32_t *first_row_dev, void *stream)
+{
+    if (!cal || !p || n < 0 || H < 1)
+        return USV_ERR_ARG;
+    if (n == 0)
+        return USV_OK;
+    if (!poses_dev || !first_row_dev || (reinterpret_cast<uintptr_t>(poses_dev) & 7) != 0)
+        return USV_ERR_ARG;
+    if (!usv::affine_ok(cal->image_to_probe))
+        return USV_ERR_ARG;
+    const double row_mm = cal->geom == USV_CONVEX ? cal->dr_mm : cal->sy_mm;
+    if (!(std::isfinite(row_mm) && row_mm > 0.0))
+        return USV_ERR_ARG;
+    const double vals[] = {p->K, p->D_mm, p->L_mm, p->spine_dir[0], p->spine_dir[1],
+                           p->spine_dir[2], p->p1_mm[0], p->p1_mm[1], p->p1_mm[2]};
+    for (double v : vals)
+        if (!std::isfinite(v))
+            return USV_ERR_ARG;
+    usv::Alg1Params ap;
+    std::memcpy(ap.K, cal->image_to_probe, sizeof(ap.K));
+    ap.k = p->K;
+    ap.d_mm = p->D_mm;
+    ap.half_l_mm = p->L_mm * 0.5;
+    for (int a = 0; a < 3; ++a) {
+        ap.dir[a] = p->spine_dir[a];
+        ap.p1[a] = p->p1_mm[a];
+    }
+    ap.row_mm = row_mm;
+    return usv::cuda_rc(usv::launch_cut_rows_alg1(poses_dev, n, H, ap, first_row_dev,
+                                                  static_cast<cudaStream_t>(stream)));
+}
+
+int usv_bone_rows_alg2(const uint8_t *images_dev, int32_t n, int32_t H, int32_t W,
+                       const usv_alg2_params *p, int32_t *bone_row_dev, int32_t *first_row_dev,
+                       void *stream)
+{
+    if (!p || n < 0 || H < 1 || W < 1)
+        return USV_ERR_ARG;
+    if (n == 0)
+        return USV_OK;
+    if (!images_dev || !bone_row_dev || !first_row_dev)
+        return USV_ERR_ARG;
+    if (H > USV_ALG2_MAX_ROWS || W > usv::kMaxDim)
+        return USV_ERR_RANGE;
+    if (p->search_from_row < 0 || p->search_from_row >= H || p->drop_rows < 1 ||
+        p->window < 1 || (p->window & 1) == 0 || p->margin_rows < 0)
+        return USV_ERR_ARG;
+    return usv::cuda_rc(usv::launch_bone_rows_alg2(images_dev, n, H, W, p->search_from_row,
+                                                   p->drop_rows, p->window, p->margin_rows,
+                                                   bone_row_dev, first_row_dev,
+                                                   static_cast<cudaStream_t>(stream)));
+}
+
+int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                     int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                     const int32_t *first_rows_dev, void *stream)
 {
     if (!vol || !cal || n < 0)
         return USV_ERR_ARG;
@@ -220,6 +297,7 @@ int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_
     }
     const bool convex = cal->geom == USV_CONVEX;
     sp.convex = convex ? 1 : 0;
+    sp.first_rows = nullptr;
     if (convex) {
         if (!(std::isfinite(cal->r0_mm) && std::isfinite(cal->dr_mm) &&
               std::isfinite(cal->sector_deg)))
@@ -250,6 +328,7 @@ int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_
         e = usv::launch_beam_setup(v.beams, W, cal->sector_deg, st);
     for (int c0 = 0; c0 < n && e == cudaSuccess; c0 += usv::kRecCap) {
         const int nc = n - c0 < usv::kRecCap ? n - c0 : usv::kRecCap;
+        sp.first_rows = first_rows_dev ? first_rows_dev + c0 : nullptr;
         e = usv::launch_frame_setup(poses_dev + (size_t)c0 * 16, nc, sp, v.rec, v.status, st);
         if (e != cudaSuccess)
             break;

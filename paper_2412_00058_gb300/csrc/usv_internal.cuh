@@ -16,7 +16,8 @@ struct FrameRec {
     double d[9];     // FP64 map; linear: same as q unquantised; convex: per-mm factors
     int valid;       // 0: frame skipped (bad pose)
     int nmax;        // upper bound on the pixels of this frame that share one voxel
-    int pad[2];
+    int first_row;   // rows above it are cut away (tissue segmentation); 0: keep all
+    int pad;
 };
 static_assert(sizeof(FrameRec) == 160, "FrameRec layout");
 
@@ -54,12 +55,22 @@ struct SetupParams {
     double sx, sy;        // linear: mm per column / row; convex: 1, 1 (per mm)
     double s[3], o[3];
     int convex;
+    const int32_t *first_rows;  // per-frame first inserted row, or null (all rows)
 };
 
 // ---- launchers (each in its own translation unit) ----
 cudaError_t launch_frame_setup(const double *poses, int n, const SetupParams &sp, FrameRec *rec,
                                uint32_t *status, cudaStream_t st);
 cudaError_t launch_beam_setup(double2 *beams, int W, double sector_deg, cudaStream_t st);
+struct Alg1Params {
+    double K[16];
+    double k, d_mm, half_l_mm, dir[3], p1[3], row_mm;
+};
+cudaError_t launch_cut_rows_alg1(const double *poses, int n, int H, const Alg1Params &p,
+                                 int32_t *first_rows, cudaStream_t st);
+cudaError_t launch_bone_rows_alg2(const uint8_t *img, int n, int H, int W, int from_row, int drop,
+                                  int window, int margin, int32_t *bone_rows, int32_t *first_rows,
+                                  cudaStream_t st);
 cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H, int W,
                               cudaStream_t st);
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,

@@ -130,6 +130,7 @@ extern "C" int usv_insert_pnn_noalloc(uint64_t *accum_dev, usv_grid grid,
     sp.sx = cal->sx_mm;
     sp.sy = cal->sy_mm;
     sp.convex = 0;
+    sp.first_rows = nullptr;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = usv::launch_frame_setup(poses_dev, n, sp, v.rec, v.status, st);
     if (e == cudaSuccess)

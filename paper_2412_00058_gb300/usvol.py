@@ -34,7 +34,8 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_insert_frames", "usv_fill_holes", "usv_project_depth_band", "usv_volume_read",
            "usv_volume_write_accum", "usv_status", "usv_strerror", "usv_last_cuda_error",
            "usv_abi_version", "usv_insert_pnn_noalloc", "usv_fill_holes_region",
-           "usv_project_depth_band_region")
+           "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
+           "usv_bone_rows_alg2")
 
 
 class UsvError(RuntimeError):
@@ -55,6 +56,18 @@ class Calibration(ctypes.Structure):
                 ("sx_mm", ctypes.c_double), ("sy_mm", ctypes.c_double),
                 ("r0_mm", ctypes.c_double), ("dr_mm", ctypes.c_double),
                 ("sector_deg", ctypes.c_double)]
+
+
+class Alg1Params(ctypes.Structure):
+    """Algorithm 1 constants: Cut_n = K |P_c1.x - P_cn.x - L/2| + D."""
+    _fields_ = [("K", ctypes.c_double), ("D_mm", ctypes.c_double), ("L_mm", ctypes.c_double),
+                ("spine_dir", ctypes.c_double * 3), ("p1_mm", ctypes.c_double * 3)]
+
+
+class Alg2Params(ctypes.Structure):
+    """Algorithm 2 settings (bone contour search and temporal median)."""
+    _fields_ = [("search_from_row", ctypes.c_int32), ("drop_rows", ctypes.c_int32),
+                ("window", ctypes.c_int32), ("margin_rows", ctypes.c_int32)]
 
 
 _lock = threading.Lock()
@@ -99,6 +112,14 @@ def lib():
             L.usv_status.restype = ctypes.c_int
             L.usv_strerror.argtypes = [ctypes.c_int]
             L.usv_strerror.restype = ctypes.c_char_p
+            L.usv_insert_frames_cut.argtypes = [P, P, I, I, I, I, P,
+                                                ctypes.POINTER(Calibration), P, P]
+            L.usv_insert_frames_cut.restype = ctypes.c_int
+            L.usv_cut_rows_alg1.argtypes = [P, I, I, ctypes.POINTER(Calibration),
+                                            ctypes.POINTER(Alg1Params), P, P]
+            L.usv_cut_rows_alg1.restype = ctypes.c_int
+            L.usv_bone_rows_alg2.argtypes = [P, I, I, I, ctypes.POINTER(Alg2Params), P, P, P]
+            L.usv_bone_rows_alg2.restype = ctypes.c_int
             L.usv_last_cuda_error.argtypes = []
             L.usv_last_cuda_error.restype = ctypes.c_char_p
             L.usv_abi_version.argtypes = []
@@ -166,6 +187,30 @@ def insert_frames(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: i
     _check(lib().usv_insert_frames(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H, W,
                                    dtype, ctypes.c_void_p(poses_ptr), ctypes.byref(cal),
                                    ctypes.c_void_p(_stream_ptr(stream))), "usv_insert_frames")
+
+
+def insert_frames_cut(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
+                      poses_ptr: int, cal: Calibration, first_rows_ptr: int, stream=None) -> None:
+    _check(lib().usv_insert_frames_cut(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H,
+                                       W, dtype, ctypes.c_void_p(poses_ptr), ctypes.byref(cal),
+                                       ctypes.c_void_p(first_rows_ptr),
+                                       ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_insert_frames_cut")
+
+
+def cut_rows_alg1(poses_ptr: int, n: int, H: int, cal: Calibration, prm: Alg1Params,
+                  first_rows_ptr: int, stream=None) -> None:
+    _check(lib().usv_cut_rows_alg1(ctypes.c_void_p(poses_ptr), n, H, ctypes.byref(cal),
+                                   ctypes.byref(prm), ctypes.c_void_p(first_rows_ptr),
+                                   ctypes.c_void_p(_stream_ptr(stream))), "usv_cut_rows_alg1")
+
+
+def bone_rows_alg2(images_ptr: int, n: int, H: int, W: int, prm: Alg2Params, bone_rows_ptr: int,
+                   first_rows_ptr: int, stream=None) -> None:
+    _check(lib().usv_bone_rows_alg2(ctypes.c_void_p(images_ptr), n, H, W, ctypes.byref(prm),
+                                    ctypes.c_void_p(bone_rows_ptr),
+                                    ctypes.c_void_p(first_rows_ptr),
+                                    ctypes.c_void_p(_stream_ptr(stream))), "usv_bone_rows_alg2")
 
 
 def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
