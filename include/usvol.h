@@ -190,6 +190,37 @@ int usv_bone_rows_alg2(const uint8_t *images_dev, int32_t n, int32_t H, int32_t 
                        void *stream);
 
 /* ------------------------------------------------------------------------
+ * Pose refinement (correcting the patient movement that long scans suffer,
+ * Sec. I and III.A): the gradient of a depth-band projection loss with
+ * respect to every frame's 6-DoF pose, through the trilinear splat.
+ *
+ * usv_pose_loss_grad -- vol must be USV_TRILINEAR, the probe USV_LINEAR,
+ *   1 <= n <= 4096.  Clears vol and inserts the frames, then
+ *     V = S / (W + eps)             (soft normalisation, differentiable)
+ *     P[y][x] = mean over z in [z_lo, z_hi) of V          -> proj_dev
+ *     L = sum (P - target)^2                              -> *loss_dev (FP64)
+ *   and, for the left perturbation of each pose about its frame centre c
+ *   (p' = R(w)(p - c) + c + t, t in mm, w a rotation vector in rad),
+ *     grad_dev[f][0..2] = dL/dt,  grad_dev[f][3..5] = dL/dw  at t = w = 0
+ *   (FP64 per frame; trilinear weights are piecewise linear: at a cell face
+ *   the derivative from the cell floor() selects).  adj_scratch_dev holds
+ *   2 * (z_hi - z_lo) * ny * nx floats.  target_dev/proj_dev: [ny][nx].
+ *
+ * usv_apply_pose_delta -- poses_out[f] = T(t) T(c) R(w) T(-c) poses[f] for
+ *   delta[f] = (t, w) (Rodrigues), c the frame centre ((W-1)sx/2, 0,
+ *   (H-1)sy/2) in world coordinates: the perturbation the gradient refers
+ *   to.  Linear probes; poses_out must not alias poses.
+ * ---------------------------------------------------------------------- */
+int usv_pose_loss_grad(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                       int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                       int32_t z_lo, int32_t z_hi, float eps, const float *target_dev,
+                       float *proj_dev, float *adj_scratch_dev, double *loss_dev,
+                       double *grad_dev, void *stream);
+int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32_t n, int32_t H,
+                         int32_t W, const usv_calibration *cal, double *poses_out_dev,
+                         void *stream);
+
+/* ------------------------------------------------------------------------
  * usv_fill_holes -- normalisation + hole filling (PNN's second stage; the
  * 3x3x3 neighbourhood is radius 1, the only radius built).  One pass that
  * reads only the accumulators, so it can be re-run after more inserts:

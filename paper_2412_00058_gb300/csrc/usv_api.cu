@@ -268,6 +268,66 @@ int usv_bone_rows_alg2(const uint8_t *images_dev, int32_t n, int32_t H, int32_t 
                                                    static_cast<cudaStream_t>(stream)));
 }
 
+int usv_pose_loss_grad(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                       int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                       int32_t z_lo, int32_t z_hi, float eps, const float *target_dev,
+                       float *proj_dev, float *adj_scratch_dev, double *loss_dev,
+                       double *grad_dev, void *stream)
+{
+    if (!vol || !cal || !target_dev || !proj_dev || !adj_scratch_dev || !loss_dev || !grad_dev)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    if (v.mode != USV_TRILINEAR || cal->geom != USV_LINEAR)
+        return USV_ERR_UNSUPPORTED;
+    if (n < 1 || n > usv::kRecCap)
+        return USV_ERR_RANGE;
+    if (z_lo < 0 || z_hi > v.g.nz || z_lo >= z_hi)
+        return USV_ERR_RANGE;
+    if (!(std::isfinite(eps) && eps > 0.0f))
+        return USV_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(adj_scratch_dev) & 7) != 0)
+        return USV_ERR_ARG;
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = usv_volume_reset(vol, stream);
+    if (rc == USV_OK)
+        rc = usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream);
+    if (rc != USV_OK)
+        return rc;
+    cudaError_t e = usv::launch_zero_f64(loss_dev, 1, st);
+    if (e == cudaSuccess)
+        e = usv::launch_zero_f64(grad_dev, 6 * n, st);
+    if (e == cudaSuccess)
+        e = usv::launch_soft_project_adjoint(v, z_lo, z_hi, eps, target_dev, proj_dev,
+                                             reinterpret_cast<float2 *>(adj_scratch_dev),
+                                             loss_dev, st);
+    if (e == cudaSuccess)
+        e = usv::launch_pose_grad(v, images_dev, dtype == USV_F32, n, H, W, z_lo, z_hi,
+                                  reinterpret_cast<const float2 *>(adj_scratch_dev), grad_dev,
+                                  st);
+    return usv::cuda_rc(e);
+}
+
+int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32_t n, int32_t H,
+                         int32_t W, const usv_calibration *cal, double *poses_out_dev,
+                         void *stream)
+{
+    if (!cal || n < 0 || H < 1 || W < 1)
+        return USV_ERR_ARG;
+    if (n == 0)
+        return USV_OK;
+    if (!poses_dev || !delta_dev || !poses_out_dev || poses_out_dev == poses_dev)
+        return USV_ERR_ARG;
+    if (cal->geom != USV_LINEAR)
+        return USV_ERR_UNSUPPORTED;
+    if (!usv::affine_ok(cal->image_to_probe))
+        return USV_ERR_ARG;
+    const double cx = 0.5 * (double)(W - 1) * cal->sx_mm, cz = 0.5 * (double)(H - 1) * cal->sy_mm;
+    return usv::cuda_rc(usv::launch_apply_pose_delta(poses_dev, delta_dev, n, cx, cz,
+                                                     cal->image_to_probe, poses_out_dev,
+                                                     static_cast<cudaStream_t>(stream)));
+}
+
 int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
                      const int32_t *first_rows_dev, void *stream)

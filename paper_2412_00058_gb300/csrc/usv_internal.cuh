@@ -84,6 +84,14 @@ cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, c
 cudaError_t launch_project_f32(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
                                float *out, uint16_t *cnt, cudaStream_t st);
 cudaError_t launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t st);
+cudaError_t launch_zero_f64(double *p, int n, cudaStream_t st);
+cudaError_t launch_soft_project_adjoint(const Volume &v, int lo, int hi, float eps,
+                                        const float *target, float *proj, float2 *adj,
+                                        double *loss, cudaStream_t st);
+cudaError_t launch_pose_grad(const Volume &v, const void *img, int is_f32, int n, int H, int W,
+                             int lo, int hi, const float2 *adj, double *grad, cudaStream_t st);
+cudaError_t launch_apply_pose_delta(const double *poses, const double *delta, int n, double cx,
+                                    double cz, const double *K, double *out, cudaStream_t st);
 cudaError_t launch_unpack_mask(const Volume &v, uint8_t *dst, cudaStream_t st);
 
 }  // namespace usv

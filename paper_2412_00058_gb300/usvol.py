@@ -35,7 +35,7 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_volume_write_accum", "usv_status", "usv_strerror", "usv_last_cuda_error",
            "usv_abi_version", "usv_insert_pnn_noalloc", "usv_fill_holes_region",
            "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
-           "usv_bone_rows_alg2")
+           "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta")
 
 
 class UsvError(RuntimeError):
@@ -120,6 +120,11 @@ def lib():
             L.usv_cut_rows_alg1.restype = ctypes.c_int
             L.usv_bone_rows_alg2.argtypes = [P, I, I, I, ctypes.POINTER(Alg2Params), P, P, P]
             L.usv_bone_rows_alg2.restype = ctypes.c_int
+            L.usv_pose_loss_grad.argtypes = [P, P, I, I, I, I, P, ctypes.POINTER(Calibration), I,
+                                             I, ctypes.c_float, P, P, P, P, P, P]
+            L.usv_pose_loss_grad.restype = ctypes.c_int
+            L.usv_apply_pose_delta.argtypes = [P, P, I, I, I, ctypes.POINTER(Calibration), P, P]
+            L.usv_apply_pose_delta.restype = ctypes.c_int
             L.usv_last_cuda_error.argtypes = []
             L.usv_last_cuda_error.restype = ctypes.c_char_p
             L.usv_abi_version.argtypes = []
@@ -211,6 +216,26 @@ def bone_rows_alg2(images_ptr: int, n: int, H: int, W: int, prm: Alg2Params, bon
                                     ctypes.c_void_p(bone_rows_ptr),
                                     ctypes.c_void_p(first_rows_ptr),
                                     ctypes.c_void_p(_stream_ptr(stream))), "usv_bone_rows_alg2")
+
+
+def pose_loss_grad(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
+                   poses_ptr: int, cal: Calibration, z_lo: int, z_hi: int, eps: float,
+                   target_ptr: int, proj_ptr: int, adj_ptr: int, loss_ptr: int, grad_ptr: int,
+                   stream=None) -> None:
+    _check(lib().usv_pose_loss_grad(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H, W,
+                                    dtype, ctypes.c_void_p(poses_ptr), ctypes.byref(cal), z_lo,
+                                    z_hi, float(eps), ctypes.c_void_p(target_ptr),
+                                    ctypes.c_void_p(proj_ptr), ctypes.c_void_p(adj_ptr),
+                                    ctypes.c_void_p(loss_ptr), ctypes.c_void_p(grad_ptr),
+                                    ctypes.c_void_p(_stream_ptr(stream))), "usv_pose_loss_grad")
+
+
+def apply_pose_delta(poses_ptr: int, delta_ptr: int, n: int, H: int, W: int, cal: Calibration,
+                     out_ptr: int, stream=None) -> None:
+    _check(lib().usv_apply_pose_delta(ctypes.c_void_p(poses_ptr), ctypes.c_void_p(delta_ptr), n, H,
+                                      W, ctypes.byref(cal), ctypes.c_void_p(out_ptr),
+                                      ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_apply_pose_delta")
 
 
 def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
