@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="usvol", choices=["usvol", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-variants", action="store_true",
+                   help="skip the trilinear convex sweep and pose-gradient timings")
     p.add_argument("--stream-seconds", type=float, default=4.0,
                    help="seconds of the four-session streaming run (0: skip)")
     p.add_argument("--frames", type=int, default=3600,
@@ -242,6 +244,72 @@ def oracle_sweep_seconds(w, frac: float, rng_offset: int = 0, acc=None):
     desc = (f"oracle insert of frames [{f0},{f0 + k}) of {n} (x{n / k:.1f}) + fill/project of "
             f"y-slab [{y0},{y0 + rows}) of {ny} (x{ny / rows:.1f}); single thread")
     return sweep, desc, t_ins + t_fp
+
+
+def measure_variants(dev, reps: int = 5):
+    """Event-timed variant rows: the full convex-fan sweep with trilinear
+    splatting (3000 frames 512x512 -> 400x1700x400), and one evaluation of
+    the pose-refinement loss + gradient (512 FP32 frames 256x256 ->
+    256x512x192)."""
+    import numpy as np
+    import torch
+    from paper_2412_00058_gb300 import posegrad, synth, usvol
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    w = synth.convex_fan()
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "trilinear", device=dev)
+    imgs = torch.from_numpy(w.images).to(dev)
+    poses = torch.from_numpy(w.poses).to(dev)
+    cal = usvol.calibration_of(w)
+    nx, ny, nz = w.grid
+    img_out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
+    cnt = torch.empty((ny, nx), dtype=torch.int16, device=dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ts = []
+    for r in range(reps + 1):
+        ev[0].record(stream)
+        vol.reset(stream)
+        ev[1].record(stream)
+        vol.insert(imgs, poses, cal, stream)
+        ev[2].record(stream)
+        vol.fill(stream)
+        vol.project(*w.band, out=img_out, count=cnt, stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize(dev)
+        if r:
+            ts.append((ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2])))
+    step = float(np.median([t[0] for t in ts]))
+    ins = float(np.median([t[1] for t in ts]))
+    samples = w.n * w.H * w.W
+    out["trilinear_convex_sweep"] = {
+        "workload": "3000 convex frames 512x512 uint8 (60 deg, 120 mm) -> 400x1700x400 @ 0.4 mm",
+        "ms_per_sweep": step, "frames_per_s": w.n / step * 1e3,
+        "insert_ms": ins, "samples_per_s": samples / ins * 1e3}
+    del vol, imgs, poses
+    torch.cuda.empty_cache()
+    w = synth.pose_refine()
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "trilinear", device=dev)
+    prob = posegrad.PoseProblem(vol, torch.from_numpy(w.images).to(dev),
+                                torch.from_numpy(w.meta["noisy_poses"]).to(dev),
+                                usvol.calibration_of(w), w.band,
+                                torch.zeros((w.grid[1], w.grid[0]), dtype=torch.float32,
+                                            device=dev), 1e-2)
+    gt = torch.from_numpy(w.poses).to(dev)
+    prob.evaluate(gt)
+    prob.target = prob.proj.clone()
+    ts = []
+    for r in range(reps + 1):
+        ev[0].record(stream)
+        prob.evaluate(prob.poses)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        if r:
+            ts.append(ev[0].elapsed_time(ev[1]))
+    out["pose_gradient"] = {
+        "workload": "512 FP32 frames 256x256 -> 256x512x192 @ 0.3 mm, band [80,140)",
+        "ms_per_loss_and_gradient": float(np.median(ts)),
+        "loss_at_noisy_poses": float(prob.loss.item())}
+    return out
 
 
 def run_reference(args):
@@ -436,6 +504,11 @@ def run_gpu(args):
                              "270x1840x200 (PNN) and 400x1700x400 (trilinear) volumes")
         del sched
 
+    # ---- variant rows: trilinear convex sweep, pose gradient (one GPU)
+    variants = None
+    if not args.no_variants and world == 1:
+        variants = measure_variants(dev)
+
     # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -469,6 +542,7 @@ def run_gpu(args):
             "p50_frame_to_render_ms": streaming["p50_ms"] if streaming else None,
             "p99_frame_to_render_ms": streaming["p99_ms"] if streaming else None,
             "streaming": streaming,
+            "variants": variants,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches_per_step * K,
             "clocks": clocks,
         }
