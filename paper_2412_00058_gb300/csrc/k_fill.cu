@@ -105,7 +105,7 @@ __device__ __forceinline__ unsigned mean_round_fast(unsigned S, unsigned C)
     return min(q, 255u);
 }
 
-__global__ void __launch_bounds__(FTX *FBY) k_fill_pnn(FillArgs a)
+__global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
 {
     constexpr int NT = FTX * FBY;
     constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries copied per thread
