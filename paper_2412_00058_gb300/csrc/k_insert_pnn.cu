@@ -6,11 +6,14 @@
 // integer, so the result is exact and independent of execution order.
 //
 // GB300 design:
-//  * one CTA = a tile of up to 256 columns x 32 rows of FPC consecutive
-//    frames; a warp covers one 256-pixel row segment, each lane eight
+//  * one CTA = a tile of up to 128 columns x 64 rows of FPC consecutive
+//    frames; a half-warp covers one 128-pixel row segment, each lane eight
 //    consecutive pixels read with one coalesced 64-bit load (the next row's
-//    load is issued before the current row is processed); warps take every
-//    8th row;
+//    load is issued before the current row is processed); the CTA's 16
+//    half-warps take every 16th row.  The near-square tile keeps the box
+//    small: the frames are tilted in plane, and an axis-aligned box around a
+//    tilted 128 x 64 patch holds about 0.09 entries per pixel against 0.13
+//    for a 256 x 32 patch;
 //  * the tile's voxel bounding box over its frames is exact (the map is
 //    affine, so the extremes sit at the tile corners), so the CTA can
 //    accumulate into a dense shared-memory box and then add each touched
@@ -39,7 +42,11 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPix = 8;              // pixels per lane per row (one 64-bit load)
-constexpr int kTileW = 32 * kPix;    // columns per tile
+constexpr int kTileW = 128;          // columns per tile
+constexpr int kRowLanes = kTileW / kPix;           // lanes per row segment
+constexpr int kWarpRows = 32 / kRowLanes;          // rows per warp per pass
+constexpr int kPassRows = kWarps * kWarpRows;      // rows per CTA per pass
+constexpr int kTileH = 64;           // rows per tile
 constexpr int kSmem = 48 * 1024;     // dynamic shared memory per CTA (the box)
 constexpr int kFpc = 8;              // frames per CTA (<= 8: warp 0 takes 4 corners x 8 frames)
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
@@ -60,28 +67,68 @@ struct PnnArgs {
 
 __device__ __forceinline__ int hi32(long long q) { return (int)(q >> 32); }
 
+// Division by a CTA-uniform d in [1, 2^16] of numerators n < 2^16:
+// with m = floor(2^32 / d) + 1 = 2^32/d + e, 0 < e <= 1,
+//     n*m / 2^32 = n/d + n*e/2^32,   n*e/2^32 < 2^-16 <= 1/d,
+// and the fractional part of n/d is at most 1 - 1/d, so floor(n*m / 2^32)
+// = floor(n/d).  (d = 1 would need m = 2^32 + 1, so it is taken apart.)
+__device__ __forceinline__ unsigned div_magic(unsigned d)
+{
+    return d > 1u ? (unsigned)(0x100000000ull / d) + 1u : 0u;
+}
+
+__device__ __forceinline__ unsigned div_by(unsigned n, unsigned d, unsigned m)
+{
+    return d > 1u ? __umulhi(n, m) : n;
+}
+
 __device__ __forceinline__ unsigned long long pack64(unsigned s, unsigned c)
 {
     return ((unsigned long long)c << 32) | (unsigned long long)s;
 }
 
+// Byte B of `word` in bits 0-7, the other bytes taken from `hi` (bytes
+// 1-3 of hi land in bytes 1-3): one byte permute gives the packed box entry
+// (count 1 << 22 | I) or, with hi = 0, the plain intensity.
+template <int B>
+__device__ __forceinline__ unsigned byte_with(unsigned word, unsigned hi)
+{
+    unsigned d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(word), "r"(hi), "n"(0x7650 | B));
+    return d;
+}
+
 // One pixel: box-local voxel from the coordinates, then the accumulate.
-template <bool CHECK, int MODE>
+template <bool CHECK, int MODE, int B>
 __device__ __forceinline__ void put(unsigned *box, unsigned cap, unsigned long long *acc,
                                     long long qx, long long qy, long long qz, unsigned ex,
-                                    unsigned ey, unsigned ez, unsigned I)
+                                    unsigned ey, unsigned ez, unsigned word)
 {
     const unsigned lx = (unsigned)hi32(qx), ly = (unsigned)hi32(qy), lz = (unsigned)hi32(qz);
     if (CHECK && !(lx < ex && ly < ey && lz < ez))
         return;
     const unsigned key = (lz * ey + ly) * ex + lx;
     if (MODE == MODE_PACKED) {
-        atomicAdd(box + key, (1u << kCountShift) | I);
+        atomicAdd(box + key, byte_with<B>(word, 1u << kCountShift));
     } else if (MODE == MODE_SPLIT) {
-        atomicAdd(box + key, I);
+        atomicAdd(box + key, byte_with<B>(word, 0u));
         atomicAdd(box + cap + key, 1u);
     } else {
-        atomicAdd(acc + key, pack64(I, 1u));
+        atomicAdd(acc + key, pack64(byte_with<B>(word, 0u), 1u));
+    }
+}
+
+template <int J, bool CHECK, int MODE>
+__device__ __forceinline__ void put_px(unsigned *box, unsigned cap, unsigned long long *acc,
+                                       long long qx, long long qy, long long qz, long long Ax,
+                                       long long Ay, long long Az, unsigned ex, unsigned ey,
+                                       unsigned ez, uint2 w, int npx)
+{
+    if constexpr (J < kPix) {
+        if (J < npx)
+            put<CHECK, MODE, J & 3>(box, cap, acc, qx, qy, qz, ex, ey, ez, J < 4 ? w.x : w.y);
+        put_px<J + 1, CHECK, MODE>(box, cap, acc, qx + Ax, qy + Ay, qz + Az, Ax, Ay, Az, ex, ey,
+                                   ez, w, npx);
     }
 }
 
@@ -91,16 +138,7 @@ __device__ __forceinline__ void put_group(unsigned *box, unsigned cap, unsigned 
                                           long long Ay, long long Az, unsigned ex, unsigned ey,
                                           unsigned ez, uint2 w, int npx)
 {
-#pragma unroll
-    for (int j = 0; j < kPix; ++j) {
-        if (j < npx) {
-            const unsigned word = j < 4 ? w.x : w.y;
-            put<CHECK, MODE>(box, cap, acc, qx, qy, qz, ex, ey, ez, (word >> (8 * (j & 3))) & 0xFFu);
-        }
-        qx += Ax;
-        qy += Ay;
-        qz += Az;
-    }
+    put_px<0, CHECK, MODE>(box, cap, acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w, npx);
 }
 
 template <bool VEC, bool CHECK, int MODE>
@@ -110,22 +148,31 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
                                            unsigned cap, const FrameRec *recs)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int u = u0 + kPix * lane;
-    if (u >= u1 || v0 + warp >= v1)
+    const int u = u0 + kPix * (lane % kRowLanes);
+    const int vs = v0 + warp * kWarpRows + lane / kRowLanes;  // this lane's first row
+    if (u >= u1 || vs >= v1)
         return;
     const int npx = VEC ? kPix : min(kPix, u1 - u);
-    const size_t rstep = (size_t)kWarps * a.W;
+    const size_t rstep = (size_t)kPassRows * a.W;
     for (int f = f0; f < f1; ++f) {
         const FrameRec *r = recs + (f - f0);
         if (!r->valid)
             continue;
         const long long Ax = r->q[0], Ay = r->q[1], Az = r->q[2];
         const long long Bx = r->q[3], By = r->q[4], Bz = r->q[5];
-        int v = v0 + warp;
+        // rows above first_row are cut away (tissue segmentation)
+        const int fr = r->first_row;
+        if (fr >= v1)
+            continue;
+        int v = vs;
+        if (v < fr)
+            v += (fr - v + kPassRows - 1) / kPassRows * kPassRows;
+        if (v >= v1)
+            continue;
         const long long qx0 = r->q[6] + off[0] + (long long)u * Ax + (long long)v * Bx;
         const long long qy0 = r->q[7] + off[1] + (long long)u * Ay + (long long)v * By;
         const long long qz0 = r->q[8] + off[2] + (long long)u * Az + (long long)v * Bz;
-        const long long Rx = kWarps * Bx, Ry = kWarps * By, Rz = kWarps * Bz;  // row step
+        const long long Rx = kPassRows * Bx, Ry = kPassRows * By, Rz = kPassRows * Bz;
         const long long Ex = (kPix - 1) * Ax, Ey = (kPix - 1) * Ay, Ez = (kPix - 1) * Az;
         long long qx = qx0, qy = qy0, qz = qz0;
         const uint8_t *src = a.img + ((size_t)f * a.H + v) * a.W + u;
@@ -146,19 +193,11 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
             return w;
         };
         uint2 w = load(src);
-        for (; v < v1; v += kWarps) {
-            const bool more = v + kWarps < v1;
+        for (; v < v1; v += kPassRows) {
+            const bool more = v + kPassRows < v1;
             uint2 wn = make_uint2(0u, 0u);
             if (more)
                 wn = load(src + rstep);
-            if (v < r->first_row) {  // cut away (tissue segmentation)
-                qx += Rx;
-                qy += Ry;
-                qz += Rz;
-                src += rstep;
-                w = wn;
-                continue;
-            }
             bool inside = true;
             if (CHECK) {
                 const long long lx = qx + Ex, ly = qy + Ey, lz = qz + Ez;
@@ -293,23 +332,27 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
                                                cap, s_rec);
     }
     __syncthreads();
-    // Flush: one warp per box row (fixed y, z), lanes along x.
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (unsigned row = warp; row < ey * ez; row += kWarps) {
-        const unsigned ly = row % ey, lz = row / ey;
-        unsigned long long *dst =
-            a.acc + ((size_t)(lz + s_lo[2]) * a.ny + (ly + s_lo[1])) * a.nx + s_lo[0];
-        const unsigned *src = box + (size_t)row * ex;
-        for (unsigned lx = lane; lx < ex; lx += 32) {
-            const unsigned e = src[lx];
-            if (mode == MODE_PACKED) {
-                if (e != 0u)
-                    atomicAdd(dst + lx, pack64(e & ((1u << kCountShift) - 1), e >> kCountShift));
-            } else {
-                const unsigned c = src[cap + lx];
-                if (c != 0u)
-                    atomicAdd(dst + lx, pack64(e, c));
-            }
+    // Flush: the box in linear order, all threads busy; each touched entry
+    // goes to HBM with one packed 64-bit atomic.  Box coordinates come from
+    // the linear index by an exact multiply-high division (below).
+    const unsigned mx = div_magic(ex), my = div_magic(ey);
+    const size_t nxy = (size_t)a.nx * a.ny;
+    unsigned long long *base =
+        a.acc + ((size_t)s_lo[2] * a.ny + s_lo[1]) * a.nx + s_lo[0];
+    for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
+        const unsigned e = box[i];
+        unsigned s, c;
+        if (mode == MODE_PACKED) {
+            s = e & ((1u << kCountShift) - 1);
+            c = e >> kCountShift;
+        } else {
+            s = e;
+            c = box[cap + i];
+        }
+        if (c != 0u) {
+            const unsigned row = div_by(i, ex, mx), lx = i - row * ex;
+            const unsigned lz = div_by(row, ey, my), ly = row - lz * ey;
+            atomicAdd(base + lz * nxy + (size_t)ly * a.nx + lx, pack64(s, c));
         }
     }
 }
@@ -331,7 +374,7 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;
-    a.th = min(32, H);
+    a.th = min(kTileH, H);
     a.tiles_x = (W + kTileW - 1) / kTileW;
     const int tiles_y = (H + a.th - 1) / a.th;
     a.fpc = kFpc;
