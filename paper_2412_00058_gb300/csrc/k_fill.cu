@@ -13,6 +13,11 @@
 // accumulators in a shared-memory ring, so every accumulator is read from
 // HBM once (plus a thin halo that neighbouring CTAs share through L2).  The
 // has-data mask is one warp ballot per 32 voxels of a row.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "usv_internal.cuh"
 
 namespace usv {
@@ -66,20 +71,30 @@ __device__ __forceinline__ void load_plane(T (*pl)[PX], const T *acc, int z, con
 // CTA: 32 x 8 threads own a 32 x 32 (x, y) column tile; thread (tx, ty)
 // owns column x0 + tx, rows y0 + 4ty .. y0 + 4ty + 3, and the CTA marches z.
 // Planes of packed accumulators (tile + 1-voxel halo) stream into a 5-slot
-// shared ring with cp.async, two planes ahead of use.  The pooled sums are
-// separable: per plane each thread forms the x-row sums of its 6 rows
-// (y-1 .. y+4) and from them the 3x3 plane sums of its 4 voxels (registers,
-// kept for three planes); the 3x3x3 sum is the sum of three plane sums, own
-// voxel included (an empty voxel adds zero).  One OR over each plane tells
-// whether it is all zero (then the tile writes zeros without arithmetic) and
-// whether any accumulator reaches 2^24 (then that output plane takes a
-// direct 64-bit path); below 2^24 every sum, and the mean's 2S + C, is exact
-// in 32 bits.
+// shared ring two planes ahead of use: one TMA tensor copy per plane
+// (cp.async.bulk.tensor, completion on an mbarrier, zero fill outside the
+// grid), or, where the grid's row pitch rules TMA out (odd nx), 8-byte
+// cp.async copies by all threads.  The pooled sums are separable: per plane
+// each thread forms the x-row sums of its 6 rows (y-1 .. y+4) and from them
+// the 3x3 plane sums of its 4 voxels (registers, kept for three planes);
+// the 3x3x3 sum is the sum of three plane sums, own voxel included (an
+// empty voxel adds zero).  One OR over each plane tells whether it is all
+// zero (then the tile writes zeros without arithmetic) and whether any
+// accumulator reaches 2^24 (then that output plane takes a direct 64-bit
+// path); below 2^24 every sum, and the mean's 2S + C, is exact in 32 bits.
 constexpr int FTX = 32, FTY = 32, FBY = 8, FRW = 4;  // FRW rows per thread
 constexpr int FPX = FTX + 2, FPY = FTY + 2, FPLANE = FPX * FPY;
 constexpr int FSLOTS = 5;
 constexpr unsigned kBig = 1u << 24;
-constexpr int kFillSmem = FSLOTS * FPLANE * 8;
+// TMA boxes start at x0 - 2 (the tensor copy's x offset must be a multiple
+// of 16 bytes = 2 entries), so a TMA plane is 36 entries wide; slots are
+// padded to 128-byte multiples.
+constexpr int kTmaW = FTX + 4;
+constexpr int kTmaBytes = kTmaW * FPY * 8;
+constexpr int kTmaSlot = (kTmaBytes + 127) / 128 * 128 / 8;  // entries per slot
+constexpr int kFillSmemCp = FSLOTS * FPLANE * 8;
+constexpr int kFillSmemTma = FSLOTS * kTmaSlot * 8;
+constexpr unsigned kSpinLimit = 1u << 22;  // bounded mbarrier waits (well over a second)
 
 __device__ __forceinline__ void cp_async8(unsigned saddr, const void *gmem, bool valid)
 {
@@ -90,6 +105,44 @@ __device__ __forceinline__ void cp_async8(unsigned saddr, const void *gmem, bool
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0u;
+}
+// true once the phase with this parity has completed; false after the limit
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
+{
+    for (unsigned i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y,
+                                            int z, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
 
 // floor(S/C + 1/2) = floor((2S + C) / 2C), clamped to 255, for S < 2^29 and
 // 0 < C < 2^29 (so N = 2S + C and D = 2C fit in 31 bits): the FP32 estimate
@@ -105,12 +158,18 @@ __device__ __forceinline__ unsigned mean_round_fast(unsigned S, unsigned C)
     return min(q, 255u);
 }
 
-__global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
+template <bool TMA>
+__global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a, const __grid_constant__ CUtensorMap map)
 {
     constexpr int NT = FTX * FBY;
-    constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries copied per thread
-    extern __shared__ __align__(16) unsigned long long Pring[];  // [FSLOTS][FPY][FPX]
+    constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries per thread (copy / OR pass)
+    constexpr int RS = TMA ? kTmaW : FPX;        // ring row stride (entries)
+    constexpr int CO = TMA ? 1 : 0;              // ring column of halo column 0
+    constexpr int SLOT = TMA ? kTmaSlot : FPLANE;
+    extern __shared__ __align__(128) unsigned long long Pring[];  // [FSLOTS][FPY][RS]
     __shared__ unsigned sflag[FSLOTS];
+    __shared__ __align__(8) unsigned long long sbar[FSLOTS];
+    __shared__ int s_abort;
     const auto *acc = static_cast<const unsigned long long *>(a.acc);
     auto *val = static_cast<uint8_t *>(a.val);
     const int x0 = a.rx0 + blockIdx.x * FTX, y0 = a.ry0 + blockIdx.y * FTY;
@@ -119,10 +178,15 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
     const int x = x0 + tx, yb = 4 * ty;  // first of this thread's rows (tile-local)
     const size_t plane = (size_t)a.nx * a.ny;
     const unsigned sbase = (unsigned)__cvta_generic_to_shared(Pring);
+    const unsigned bbase = (unsigned)__cvta_generic_to_shared(sbar);
     bool saturated = false;
+    unsigned phase = 0u;      // TMA: parity of each slot's next completion
+    unsigned pending = 0u;    // TMA, thread 0: slots with a copy in flight
 
+    // this thread's entries of the plane for the copy and OR passes
     size_t goff[PER];
     bool gok[PER];
+    int soff[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int i = tid + k * NT;
@@ -130,21 +194,50 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
         const int X = x0 - 1 + lx, Y = y0 - 1 + ly;
         gok[k] = i < FPLANE && X >= 0 && X < a.nx && Y >= 0 && Y < a.ny;
         goff[k] = gok[k] ? (size_t)Y * a.nx + X : 0;
+        soff[k] = ly * RS + lx + CO;
     }
     auto issue = [&](int pl) {
-        if (pl <= z1) {
-            const unsigned dst = sbase + (unsigned)(((pl + FSLOTS) % FSLOTS) * FPLANE * 8);
-            const bool zok = pl >= 0 && pl < a.nz;
-            const unsigned long long *base = acc + (zok ? (size_t)pl * plane : 0);
+        if (TMA) {
+            if (tid == 0 && pl <= z1) {
+                const int s = (pl + FSLOTS) % FSLOTS;
+                mbar_expect_tx(bbase + 8u * s, kTmaBytes);
+                // outside the grid (x < 0, y < 0, z < 0, beyond the far
+                // faces) the copy writes zeros
+                tma_load_3d(sbase + (unsigned)(s * SLOT * 8), &map, x0 - 2, y0 - 1, pl,
+                            bbase + 8u * s);
+                pending |= 1u << s;
+            }
+        } else {
+            if (pl <= z1) {
+                const unsigned dst = sbase + (unsigned)(((pl + FSLOTS) % FSLOTS) * SLOT * 8);
+                const bool zok = pl >= 0 && pl < a.nz;
+                const unsigned long long *base = acc + (zok ? (size_t)pl * plane : 0);
 #pragma unroll
-            for (int k = 0; k < PER; ++k)
-                if (tid + k * NT < FPLANE)
-                    cp_async8(dst + 8u * (tid + k * NT), base + goff[k], zok && gok[k]);
+                for (int k = 0; k < PER; ++k)
+                    if (tid + k * NT < FPLANE)
+                        cp_async8(dst + 8u * soff[k], base + goff[k], zok && gok[k]);
+            }
+            cp_async_commit();
         }
-        cp_async_commit();
     };
+    // TMA writes whole 128-byte-aligned slots; a ring that is not aligned is
+    // refused (reported as a failed wait) before any copy is issued
+    if (TMA && (sbase & 127u) != 0u) {
+        if (tid == 0)
+            atomicOr(a.status, USV_STATUS_TIMEOUT);
+        return;
+    }
     if (tid < FSLOTS)
         sflag[tid] = 0u;
+    if (tid == 0) {
+        s_abort = 0;
+        if (TMA) {
+            for (int s = 0; s < FSLOTS; ++s)
+                mbar_init(bbase + 8u * s, 1u);
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        }
+    }
     __syncthreads();
 
     // 3x3 plane sums (S, C) of this thread's rows; plane p lives in slot p % 3
@@ -164,21 +257,32 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
     const size_t mplane = (size_t)a.ny * a.nxw;
     const int nrows = min(FRW, a.ny - (y0 + yb));  // rows of this thread inside the grid
 
+    // returns false when the CTA gives up (a TMA wait ran out)
     auto step = [&](int pl, int slot, uint2(&Bn)[FRW], int &nzn, int &bign) {
         issue(pl + 2);
-        cp_async_wait<2>();
-        const unsigned long long *Pp = Pring + slot * FPLANE;
+        if (TMA) {
+            if (!mbar_wait(bbase + 8u * slot, (phase >> slot) & 1u)) {
+                s_abort = 1;
+                atomicOr(a.status, USV_STATUS_TIMEOUT);
+            }
+            phase ^= 1u << slot;
+            if (tid == 0)
+                pending &= ~(1u << slot);
+        } else {
+            cp_async_wait<2>();
+        }
+        const unsigned long long *Pp = Pring + slot * SLOT;
         unsigned orv = 0u;
 #pragma unroll
         for (int k = 0; k < PER; ++k)
             if (tid + k * NT < FPLANE) {
-                const unsigned long long w = Pp[tid + k * NT];  // own copies: visible
+                const unsigned long long w = Pp[soff[k]];
                 orv |= (unsigned)w | (unsigned)(w >> 32);
             }
         orv = __reduce_or_sync(0xFFFFFFFFu, orv);
         if (tx == 0 && orv)
             atomicOr(&sflag[slot], orv);
-        __syncthreads();
+        __syncthreads();  // the plane has landed for every thread; flags complete
         const unsigned fl = sflag[slot];
         if (tid == 0)
             sflag[slot == 0 ? FSLOTS - 1 : slot - 1] = 0u;  // read by everyone last step
@@ -191,7 +295,7 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
             uint2 Rw[FRW + 2];
 #pragma unroll
             for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 = halo rows yb .. yb+5
-                const unsigned long long *row = Pp + (yb + k) * FPX + tx;
+                const unsigned long long *row = Pp + (yb + k) * RS + tx + CO;
                 const unsigned long long p0 = row[0], p1 = row[1], p2 = row[2];
                 Rw[k] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
                                    (unsigned)(p0 >> 32) + (unsigned)(p1 >> 32) +
@@ -205,7 +309,7 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
         const int z = pl - 1;
         if (z >= z0) {
             const int sz = slot == 0 ? FSLOTS - 1 : slot - 1;  // plane z
-            const unsigned long long *Pz = Pring + sz * FPLANE;
+            const unsigned long long *Pz = Pring + sz * SLOT;
             const bool any = nzf[0] | nzf[1] | nzf[2];
             const bool big = bigf[0] | bigf[1] | bigf[2];
 #pragma unroll
@@ -213,7 +317,7 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
                 unsigned v = 0;
                 bool has = false;
                 if (any && !big) {
-                    const unsigned long long own = Pz[(yb + r + 1) * FPX + tx + 1];
+                    const unsigned long long own = Pz[(yb + r + 1) * RS + tx + 1 + CO];
                     const unsigned c_own = (unsigned)(own >> 32);
                     // own samples if any, else the pooled neighbours (the own
                     // count is 0 then; its sum is dropped so only neighbours pool)
@@ -223,17 +327,18 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
                     has = C != 0u;
                     v = mean_round_fast(S, has ? C : 1u);
                 } else if (any) {
-                    const unsigned long long own = Pz[(yb + r + 1) * FPX + tx + 1];
+                    const unsigned long long own = Pz[(yb + r + 1) * RS + tx + 1 + CO];
                     unsigned long long S = own & 0xFFFFFFFFull, C = own >> 32;
                     saturated |= C >= (1ull << 24);
                     if (C == 0) {
                         S = 0ull - (own & 0xFFFFFFFFull);  // the centre is not a neighbour
                         for (int dz = 0; dz < 3; ++dz) {
                             const unsigned long long *Pd =
-                                Pring + ((sz + FSLOTS - 1 + dz) % FSLOTS) * FPLANE;
+                                Pring + ((sz + FSLOTS - 1 + dz) % FSLOTS) * SLOT;
                             for (int dy = 0; dy < 3; ++dy)
                                 for (int dx = 0; dx < 3; ++dx) {
-                                    const unsigned long long w = Pd[(yb + r + dy) * FPX + tx + dx];
+                                    const unsigned long long w =
+                                        Pd[(yb + r + dy) * RS + tx + dx + CO];
                                     S += w & 0xFFFFFFFFull;
                                     C += w >> 32;
                                 }
@@ -254,25 +359,36 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a)
             mout += mplane;
         }
         __syncthreads();  // ring slot reuse
+        return !(TMA && s_abort);
     };
 
     issue(z0 - 1);
     issue(z0);
     int slot = (z0 - 1 + FSLOTS) % FSLOTS;
+    bool ok = true;
     // plane p's sums go to B[(p - z0 + 1) % 3]; unrolled by 3 so the slot is static
-    for (int pl = z0 - 1; pl <= z1; pl += 3) {
-        step(pl, slot, B[0], nzf[0], bigf[0]);
+    for (int pl = z0 - 1; pl <= z1 && ok; pl += 3) {
+        ok = step(pl, slot, B[0], nzf[0], bigf[0]);
         slot = slot + 1 == FSLOTS ? 0 : slot + 1;
-        if (pl + 1 > z1)
+        if (!ok || pl + 1 > z1)
             break;
-        step(pl + 1, slot, B[1], nzf[1], bigf[1]);
+        ok = step(pl + 1, slot, B[1], nzf[1], bigf[1]);
         slot = slot + 1 == FSLOTS ? 0 : slot + 1;
-        if (pl + 2 > z1)
+        if (!ok || pl + 2 > z1)
             break;
-        step(pl + 2, slot, B[2], nzf[2], bigf[2]);
+        ok = step(pl + 2, slot, B[2], nzf[2], bigf[2]);
         slot = slot + 1 == FSLOTS ? 0 : slot + 1;
     }
-    cp_async_wait<0>();
+    if (TMA) {
+        // after a timeout: wait (bounded) for the copies still in flight, so
+        // none lands in shared memory after the CTA has gone
+        if (tid == 0)
+            for (int s = 0; s < FSLOTS; ++s)
+                if (pending & (1u << s))
+                    mbar_wait(bbase + 8u * s, (phase >> s) & 1u);
+    } else {
+        cp_async_wait<0>();
+    }
     if (__syncthreads_or(saturated) && tid == 0)
         atomicOr(a.status, USV_STATUS_SATURATED);
 }
@@ -349,6 +465,44 @@ dim3 fill_grid(FillArgs &a, int tx, int ty, int waves_ctas, const int *lo, const
 
 }  // namespace
 
+namespace {
+
+// cuTensorMapEncodeTiled from the driver, looked up once
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The accumulators as a 3D tensor of u64 (x fastest) with a 36 x 34 x 1 box.
+// TMA needs 16-byte row and plane pitches, i.e. an even nx.
+bool acc_tensor_map(const Volume &v, CUtensorMap *map)
+{
+    if (v.g.nx % 2 != 0 || (reinterpret_cast<uintptr_t>(v.acc) & 15) != 0)
+        return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
+    if (!enc)
+        return false;
+    const cuuint64_t dim[3] = {(cuuint64_t)v.g.nx, (cuuint64_t)v.g.ny, (cuuint64_t)v.g.nz};
+    const cuuint64_t stride[2] = {(cuuint64_t)v.g.nx * 8, (cuuint64_t)v.g.nx * v.g.ny * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)kTmaW, (cuuint32_t)FPY, 1u};
+    const cuuint32_t estride[3] = {1u, 1u, 1u};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, v.acc, dim, stride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
 cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st)
 {
     FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0};
@@ -360,13 +514,22 @@ cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaS
     int dev = -1;
     cudaGetDevice(&dev);
     if (attr_device != dev) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_fill_pnn, cudaFuncAttributeMaxDynamicSharedMemorySize, kFillSmem);
+        cudaError_t e = cudaFuncSetAttribute(
+            k_fill_pnn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFillSmemCp);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fill_pnn<true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kFillSmemTma);
         if (e != cudaSuccess)
             return e;
         attr_device = dev;
     }
-    k_fill_pnn<<<grid, dim3(FTX, FBY), kFillSmem, st>>>(a);
+    alignas(64) CUtensorMap map;
+    if (acc_tensor_map(v, &map)) {
+        k_fill_pnn<true><<<grid, dim3(FTX, FBY), kFillSmemTma, st>>>(a, map);
+    } else {
+        std::memset(&map, 0, sizeof(map));
+        k_fill_pnn<false><<<grid, dim3(FTX, FBY), kFillSmemCp, st>>>(a, map);
+    }
     return cudaGetLastError();
 }
 

@@ -144,6 +144,38 @@ def test_fill_and_projection_on_hand_built_accumulators():
         assert np.array_equal(vol.read(usvol.READ_MASK).cpu().numpy(), oh)
 
 
+def test_fill_large_accumulators_both_plane_loaders():
+    """Counts at and above 2^24 (the fill's 64-bit path and the saturation
+    flag) next to ordinary planes, on an even nx (planes arrive by tensor
+    copies) and an odd nx (per-entry asynchronous copies): both equal the
+    oracle bit for bit."""
+    import torch
+    import oracle
+    from paper_2412_00058_gb300 import usvol
+    rng = np.random.default_rng(31)
+    for grid in [(64, 37, 9), (63, 37, 9), (96, 70, 5)]:
+        nx, ny, nz = grid
+        c = np.where(rng.random((nz, ny, nx)) < 0.4, rng.integers(1, 40, (nz, ny, nx)), 0)
+        big = rng.random((nz, ny, nx)) < 0.02
+        big[nz // 2] = False            # a plane far from any large count
+        big[:, :, : nx // 3] = False    # columns whose neighbourhood stays small
+        c = np.where(big, rng.integers(1 << 23, 1 << 26, (nz, ny, nx)), c)
+        s = (c * rng.integers(0, 64, (nz, ny, nx))).astype(np.uint64)
+        assert int(s.max()) < 1 << 32
+        c = c.astype(np.uint32)
+        packed = (c.astype(np.uint64) << np.uint64(32)) | s
+        vol = usvol.Volume(grid, (0.5, 0.5, 0.5), (0, 0, 0), "pnn")
+        src = torch.from_numpy(packed.view(np.int64)).cuda()
+        usvol.volume_write_accum(vol.handle, src.data_ptr())
+        vol.fill()
+        ov, oh = oracle.fill_pnn(s, c)
+        assert np.array_equal(vol.read(usvol.READ_VALUES).cpu().numpy(), ov)
+        assert np.array_equal(vol.read(usvol.READ_MASK).cpu().numpy(), oh)
+        saturated = bool((c >= (1 << 24)).any())
+        assert bool(vol.status() & usvol.STATUS_SATURATED) == saturated
+        assert not vol.status() & usvol.STATUS_TIMEOUT
+
+
 def test_argument_errors_with_a_live_volume():
     import torch
     from paper_2412_00058_gb300 import synth, usvol
