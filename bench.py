@@ -514,7 +514,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        sweep_s, desc, cpu_work = oracle_sweep_seconds(w, 0.25)
+        # the whole sweep (about 10 s of single-thread CPU work), no scaling
+        sweep_s, desc, cpu_work = oracle_sweep_seconds(w, 1.0)
         cpu = {"value": w.n / sweep_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
                "sample": f"{desc}; {cpu_work:.1f} s of CPU work"}
 
