@@ -65,6 +65,12 @@ typedef enum {
     USV_TRILINEAR = 1 /* trilinear splat, FP32 weighted sum + weight                    */
 } usv_mode;
 
+/* Flag OR-ed into the mode of usv_volume_bytes() / usv_volume_create(): the
+ * storage also holds a spare set of accumulators, which lets
+ * usv_fill_holes_and_clear() clear the accumulators inside the fill pass
+ * (no counterpart in the paper; costs 8 B per voxel of extra storage). */
+#define USV_SPARE_ACCUM 0x100
+
 typedef enum { USV_LINEAR = 0, USV_CONVEX = 1 } usv_geom;
 typedef enum { USV_U8 = 0, USV_F32 = 1 } usv_dtype;
 
@@ -83,7 +89,8 @@ typedef struct {
 /* ------------------------------------------------------------------------
  * usv_volume_bytes -- device bytes a volume needs: accumulators, filled
  * values, has-data bit mask, per-frame set-up scratch and the status word.
- * PNN: 8 B + 1 B + 1/8 B per voxel (+ ~0.6 MB); trilinear: 8 + 4 + 1/8.
+ * PNN: 8 B + 1 B + 1/8 B per voxel (+ ~0.6 MB); trilinear: 8 + 4 + 1/8;
+ * with USV_SPARE_ACCUM in `mode`, 8 B more per voxel.
  * Returns 0 if the grid is invalid (any n < 1, or more than 2^31-1 voxels).
  * ---------------------------------------------------------------------- */
 size_t usv_volume_bytes(usv_grid grid, int32_t mode);
@@ -231,6 +238,19 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
  * Writes the value volume and the has-data bit mask.
  * ---------------------------------------------------------------------- */
 int usv_fill_holes(usv_volume *vol, int32_t radius, void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_fill_holes_and_clear -- usv_fill_holes(), after which the volume's
+ * accumulators are zero, as after usv_volume_reset(): the call for the end
+ * of a sweep, when the next sweep starts from an empty volume (no
+ * counterpart in the paper).  With USV_SPARE_ACCUM in USV_PNN mode the fill
+ * kernel writes zeros into the spare accumulators while it reads the
+ * current ones, and the two sets swap: the clearing costs no separate pass
+ * over memory.  Otherwise it is usv_fill_holes() followed by
+ * usv_volume_reset().  Same arguments, errors and outputs as
+ * usv_fill_holes(); usv_volume_read(USV_READ_ACCUM) afterwards reads zeros.
+ * ---------------------------------------------------------------------- */
+int usv_fill_holes_and_clear(usv_volume *vol, int32_t radius, void *stream);
 
 /* ------------------------------------------------------------------------
  * usv_project_depth_band -- the VPI spine view (Sec. III.B): for every

@@ -50,6 +50,7 @@ struct FillArgs {
     uint32_t *status;
     int nx, ny, nz, nxw, zchunk;
     int rx0, ry0, rz0, rz1;  // refreshed region: x from rx0 (a multiple of 32), y from ry0, z in [rz0, rz1)
+    unsigned long long *clear;  // PNN, whole grid: accumulators to zero in the same pass, or null
 };
 
 template <typename T>
@@ -92,8 +93,11 @@ constexpr unsigned kBig = 1u << 24;
 constexpr int kTmaW = FTX + 4;
 constexpr int kTmaBytes = kTmaW * FPY * 8;
 constexpr int kTmaSlot = (kTmaBytes + 127) / 128 * 128 / 8;  // entries per slot
+// Clearing with TMA stores a zero tile of 32 x 16 entries, twice per plane.
+constexpr int kZeroRows = 16;
+constexpr int kZeroBytes = FTX * kZeroRows * 8;
 constexpr int kFillSmemCp = FSLOTS * FPLANE * 8;
-constexpr int kFillSmemTma = FSLOTS * kTmaSlot * 8;
+constexpr int kFillSmemTma = FSLOTS * kTmaSlot * 8 + kZeroBytes;
 constexpr unsigned kSpinLimit = 1u << 22;  // bounded mbarrier waits (well over a second)
 
 __device__ __forceinline__ void cp_async8(unsigned saddr, const void *gmem, bool valid)
@@ -144,6 +148,16 @@ __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map
         : "memory");
 }
 
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, int x, int y, int z,
+                                             unsigned src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group"
+                 " [%0, {%1, %2, %3}], [%4];" ::"l"(reinterpret_cast<unsigned long long>(map)),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
 // floor(S/C + 1/2) = floor((2S + C) / 2C), clamped to 255, for S < 2^29 and
 // 0 < C < 2^29 (so N = 2S + C and D = 2C fit in 31 bits): the FP32 estimate
 // of N/D is within one of the true quotient (|error| < 2^-21 relative, the
@@ -159,7 +173,9 @@ __device__ __forceinline__ unsigned mean_round_fast(unsigned S, unsigned C)
 }
 
 template <bool TMA>
-__global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a, const __grid_constant__ CUtensorMap map)
+__global__ void __launch_bounds__(FTX *FBY, 4)
+    k_fill_pnn(FillArgs a, const __grid_constant__ CUtensorMap map,
+               const __grid_constant__ CUtensorMap clear_map)
 {
     constexpr int NT = FTX * FBY;
     constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries per thread (copy / OR pass)
@@ -226,6 +242,13 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a, const __gr
         if (tid == 0)
             atomicOr(a.status, USV_STATUS_TIMEOUT);
         return;
+    }
+    // the zero tile that TMA stores into the accumulators being cleared
+    const unsigned zbase = sbase + (unsigned)(FSLOTS * SLOT * 8);
+    if (TMA && a.clear) {
+        for (int i = tid; i < kZeroBytes / 16; i += NT)
+            reinterpret_cast<uint4 *>(Pring + FSLOTS * SLOT)[i] = make_uint4(0u, 0u, 0u, 0u);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the copies
     }
     if (tid < FSLOTS)
         sflag[tid] = 0u;
@@ -307,6 +330,21 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a, const __gr
                                    Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
         }
         const int z = pl - 1;
+        if (z >= z0 && a.clear) {
+            // this tile of plane z in the accumulators being cleared; every
+            // voxel of the grid lies in exactly one (tile, plane)
+            if (TMA) {
+                if (tid == 0) {
+                    tma_store_3d(&clear_map, x0, y0, z, zbase);
+                    if (y0 + kZeroRows < a.ny)
+                        tma_store_3d(&clear_map, x0, y0 + kZeroRows, z, zbase);
+                }
+            } else if (xin) {
+                unsigned long long *c = a.clear + ((size_t)z * a.ny + y0 + yb) * a.nx + x;
+                for (int r = 0; r < nrows; ++r)
+                    c[(size_t)r * a.nx] = 0ull;
+            }
+        }
         if (z >= z0) {
             const int sz = slot == 0 ? FSLOTS - 1 : slot - 1;  // plane z
             const unsigned long long *Pz = Pring + sz * SLOT;
@@ -386,6 +424,8 @@ __global__ void __launch_bounds__(FTX *FBY, 4) k_fill_pnn(FillArgs a, const __gr
             for (int s = 0; s < FSLOTS; ++s)
                 if (pending & (1u << s))
                     mbar_wait(bbase + 8u * s, (phase >> s) & 1u);
+        if (tid == 0 && a.clear)
+            asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the zero stores
     } else {
         cp_async_wait<0>();
     }
@@ -482,20 +522,22 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled()
     return fn;
 }
 
-// The accumulators as a 3D tensor of u64 (x fastest) with a 36 x 34 x 1 box.
-// TMA needs 16-byte row and plane pitches, i.e. an even nx.
-bool acc_tensor_map(const Volume &v, CUtensorMap *map)
+// Accumulators as a 3D tensor of u64 (x fastest): a 36 x 34 x 1 box to load
+// planes, a 32 x 16 x 1 box to clear.  TMA needs 16-byte row and plane
+// pitches, i.e. an even nx.
+bool acc_tensor_map(const Volume &v, const void *acc, int box_x, int box_y, CUtensorMap *map)
 {
-    if (v.g.nx % 2 != 0 || (reinterpret_cast<uintptr_t>(v.acc) & 15) != 0)
+    if (v.g.nx % 2 != 0 || (reinterpret_cast<uintptr_t>(acc) & 15) != 0)
         return false;
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
     if (!enc)
         return false;
     const cuuint64_t dim[3] = {(cuuint64_t)v.g.nx, (cuuint64_t)v.g.ny, (cuuint64_t)v.g.nz};
     const cuuint64_t stride[2] = {(cuuint64_t)v.g.nx * 8, (cuuint64_t)v.g.nx * v.g.ny * 8};
-    const cuuint32_t box[3] = {(cuuint32_t)kTmaW, (cuuint32_t)FPY, 1u};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 1u};
     const cuuint32_t estride[3] = {1u, 1u, 1u};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, v.acc, dim, stride, box, estride,
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void *>(acc), dim, stride, box,
+               estride,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
@@ -503,9 +545,14 @@ bool acc_tensor_map(const Volume &v, CUtensorMap *map)
 
 }  // namespace
 
-cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st)
+cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st,
+                            void *clear)
 {
-    FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0};
+    FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0,
+               static_cast<unsigned long long *>(clear)};
+    if (clear && (lo[0] != 0 || lo[1] != 0 || lo[2] != 0 || hi[0] != v.g.nx ||
+                  hi[1] != v.g.ny || hi[2] != v.g.nz))
+        return cudaErrorInvalidValue;  // clearing covers the whole grid only
     // ~6 waves of 4 resident CTAs per SM; slabs of at least 16 planes
     const dim3 grid = fill_grid(a, FTX, FTY, 4 * 6, lo, hi, v.num_sms, 16);
     if (grid.x == 0 || grid.y == 0 || grid.z == 0)
@@ -523,12 +570,14 @@ cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaS
             return e;
         attr_device = dev;
     }
-    alignas(64) CUtensorMap map;
-    if (acc_tensor_map(v, &map)) {
-        k_fill_pnn<true><<<grid, dim3(FTX, FBY), kFillSmemTma, st>>>(a, map);
+    alignas(64) CUtensorMap map, cmap;
+    std::memset(&cmap, 0, sizeof(cmap));
+    if (acc_tensor_map(v, v.acc, kTmaW, FPY, &map) &&
+        (!clear || acc_tensor_map(v, clear, FTX, kZeroRows, &cmap))) {
+        k_fill_pnn<true><<<grid, dim3(FTX, FBY), kFillSmemTma, st>>>(a, map, cmap);
     } else {
         std::memset(&map, 0, sizeof(map));
-        k_fill_pnn<false><<<grid, dim3(FTX, FBY), kFillSmemCp, st>>>(a, map);
+        k_fill_pnn<false><<<grid, dim3(FTX, FBY), kFillSmemCp, st>>>(a, map, cmap);
     }
     return cudaGetLastError();
 }

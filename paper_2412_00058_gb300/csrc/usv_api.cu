@@ -5,6 +5,8 @@
 #include <cstring>
 #include <new>
 
+#include <utility>
+
 #include "usv_internal.cuh"
 
 namespace usv {
@@ -75,7 +77,7 @@ Layout layout_for(usv_grid g, int mode)
     L.acc = off;
     off += align_up(n * 8);
     L.val = off;
-    off += align_up(n * (mode == USV_PNN ? 1 : 4));
+    off += align_up(n * ((mode & ~USV_SPARE_ACCUM) == USV_PNN ? 1 : 4));
     L.mask = off;
     off += align_up((size_t)g.nz * g.ny * nxw * 4);
     L.rec = off;
@@ -84,6 +86,11 @@ Layout layout_for(usv_grid g, int mode)
     off += align_up((size_t)kBeamCap * sizeof(double2));
     L.status = off;
     off += kAlign;
+    L.spare = 0;
+    if (mode & USV_SPARE_ACCUM) {
+        L.spare = off;
+        off += align_up(n * 8);
+    }
     L.total = off;
     return L;
 }
@@ -114,7 +121,8 @@ const char *usv_strerror(int code)
 
 size_t usv_volume_bytes(usv_grid grid, int32_t mode)
 {
-    if (!usv::grid_ok(grid) || (mode != USV_PNN && mode != USV_TRILINEAR))
+    const int32_t base = mode & ~USV_SPARE_ACCUM;
+    if (!usv::grid_ok(grid) || (base != USV_PNN && base != USV_TRILINEAR))
         return 0;
     return usv::layout_for(grid, mode).total;
 }
@@ -125,7 +133,8 @@ int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double or
     if (!out)
         return USV_ERR_ARG;
     *out = nullptr;
-    if (!usv::grid_ok(grid) || (mode != USV_PNN && mode != USV_TRILINEAR))
+    const int32_t base_mode = mode & ~USV_SPARE_ACCUM;
+    if (!usv::grid_ok(grid) || (base_mode != USV_PNN && base_mode != USV_TRILINEAR))
         return USV_ERR_ARG;
     if (!usv::finite3(spacing_mm) || !usv::finite3(origin_mm))
         return USV_ERR_ARG;
@@ -153,10 +162,11 @@ int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double or
         v->spacing[a] = spacing_mm[a];
         v->origin[a] = origin_mm[a];
     }
-    v->mode = mode;
+    v->mode = base_mode;
     v->base = static_cast<char *>(device_storage);
     v->bytes = storage_bytes;
     v->acc = v->base + L.acc;
+    v->spare = L.spare ? v->base + L.spare : nullptr;
     v->val = v->base + L.val;
     v->mask = reinterpret_cast<uint32_t *>(v->base + L.mask);
     v->nxw = (grid.nx + 31) / 32;
@@ -185,7 +195,7 @@ int usv_volume_reset(usv_volume *vol, void *stream)
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const usv::Layout L = usv::layout_for(v.g, v.mode);
-    cudaError_t e = usv::launch_zero(v.acc, L.val - L.acc, v.num_sms, st);
+    cudaError_t e = usv::launch_zero(v.acc, L.val - L.acc, v.num_sms, st);  // = the spare's size
     if (e == cudaSuccess)
         e = usv::launch_zero(v.status, usv::kAlign, v.num_sms, st);
     return usv::cuda_rc(e);
@@ -411,6 +421,28 @@ int usv_fill_holes(usv_volume *vol, int32_t radius, void *stream)
     const Volume &v = *reinterpret_cast<Volume *>(vol);
     const int32_t lo[3] = {0, 0, 0}, hi[3] = {v.g.nx, v.g.ny, v.g.nz};
     return usv_fill_holes_region(vol, lo, hi, radius, stream);
+}
+
+int usv_fill_holes_and_clear(usv_volume *vol, int32_t radius, void *stream)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    if (radius != 1)
+        return USV_ERR_UNSUPPORTED;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    if (v.mode != USV_PNN || !v.spare) {
+        const int rc = usv_fill_holes(vol, radius, stream);
+        return rc != USV_OK ? rc : usv_volume_reset(vol, stream);
+    }
+    const int lo[3] = {0, 0, 0}, hi[3] = {v.g.nx, v.g.ny, v.g.nz};
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the fill reads every accumulator of `acc` and writes a zero into every
+    // one of `spare`; later work on the stream sees the zeroed set
+    const int rc = usv::cuda_rc(usv::launch_fill_pnn(v, lo, hi, st, v.spare));
+    if (rc == USV_OK)
+        std::swap(v.acc, v.spare);
+    return rc;
 }
 
 int usv_fill_holes_region(usv_volume *vol, const int32_t lo[3], const int32_t hi[3],

@@ -30,6 +30,7 @@ struct Volume {
     char *base;
     size_t bytes;
     void *acc;          // PNN: unsigned long long[N]; trilinear: float2[N] (S, W)
+    void *spare;        // USV_SPARE_ACCUM: a second accumulator set (swaps with acc), or null
     void *val;          // PNN: uint8_t[N]; trilinear: float[N]
     uint32_t *mask;     // [nz][ny][nxw] bit words, bit x%32 of word x/32
     int nxw;
@@ -45,9 +46,9 @@ constexpr int kBeamCap = 32768;    // max W
 constexpr int kMaxDim = 32768;     // max H, W
 
 struct Layout {
-    size_t acc, val, mask, rec, beams, status, total;
+    size_t acc, val, mask, rec, beams, status, spare, total;  // spare: 0 if none
 };
-Layout layout_for(usv_grid g, int mode);
+Layout layout_for(usv_grid g, int mode);  // mode may carry USV_SPARE_ACCUM
 
 // Set-up parameters passed by value to k_frame_setup.
 struct SetupParams {
@@ -77,7 +78,8 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
                                     int W, int convex, double r0, double dr, cudaStream_t st);
 // fill / project a region: voxels [lo, hi) (clipped to the grid; the fill
 // needs lo[0] a multiple of 32), columns [rlo, rhi)
-cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st);
+cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st,
+                            void *clear = nullptr);  // clear: accumulators to zero in the pass
 cudaError_t launch_fill_trilinear(const Volume &v, const int *lo, const int *hi, cudaStream_t st);
 cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
                               float *out, uint16_t *cnt, cudaStream_t st);

@@ -25,6 +25,7 @@ LIB_PATH = os.path.join(_PKG, "libusvol.so")
 OK, ERR_ARG, ERR_RANGE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 STATUS_BAD_POSE, STATUS_SATURATED, STATUS_TIMEOUT = 0x1, 0x2, 0x4
 PNN, TRILINEAR = 0, 1
+SPARE_ACCUM = 0x100
 LINEAR, CONVEX = 0, 1
 U8, F32 = 0, 1
 READ_ACCUM, READ_VALUES, READ_MASK = 0, 1, 2
@@ -35,7 +36,8 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_volume_write_accum", "usv_status", "usv_strerror", "usv_last_cuda_error",
            "usv_abi_version", "usv_insert_pnn_noalloc", "usv_fill_holes_region",
            "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
-           "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta")
+           "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta",
+           "usv_fill_holes_and_clear")
 
 
 class UsvError(RuntimeError):
@@ -243,6 +245,12 @@ def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
                                 ctypes.c_void_p(_stream_ptr(stream))), "usv_fill_holes")
 
 
+def fill_holes_and_clear(handle: int, radius: int = 1, stream=None) -> None:
+    _check(lib().usv_fill_holes_and_clear(ctypes.c_void_p(handle), radius,
+                                          ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_fill_holes_and_clear")
+
+
 def project_depth_band(handle: int, z_lo: int, z_hi: int, out_ptr: int, count_ptr: int | None,
                        stream=None) -> None:
     _check(lib().usv_project_depth_band(ctypes.c_void_p(handle), z_lo, z_hi,
@@ -291,16 +299,20 @@ def status(handle: int, stream=None) -> int:
 class Volume:
     """A reconstruction volume in torch-owned device storage."""
 
-    def __init__(self, grid, spacing, origin=(0.0, 0.0, 0.0), mode="pnn", device="cuda"):
+    def __init__(self, grid, spacing, origin=(0.0, 0.0, 0.0), mode="pnn", device="cuda",
+                 spare=False):
+        """spare=True adds a second accumulator set (USV_SPARE_ACCUM), so that
+        fill_and_clear() clears the accumulators inside the fill pass."""
         self.grid = tuple(int(g) for g in grid)
         self.mode = _mode(mode)
         self.spacing = tuple(float(s) for s in spacing)
         self.origin = tuple(float(o) for o in origin)
-        nbytes = volume_bytes(self.grid, self.mode)
+        flags = self.mode | (SPARE_ACCUM if spare else 0)
+        nbytes = volume_bytes(self.grid, flags)
         if nbytes == 0:
             raise UsvError(ERR_ARG, f"invalid grid {self.grid}")
         self.storage = torch.empty(nbytes, dtype=torch.uint8, device=device)
-        self.handle = volume_create(self.grid, self.spacing, self.origin, self.mode,
+        self.handle = volume_create(self.grid, self.spacing, self.origin, flags,
                                     self.storage.data_ptr(), nbytes)
 
     def __del__(self):
@@ -331,6 +343,10 @@ class Volume:
 
     def fill(self, stream=None):
         fill_holes(self.handle, 1, stream)
+
+    def fill_and_clear(self, stream=None):
+        """fill(), then the accumulators read as zero (end of a sweep)."""
+        fill_holes_and_clear(self.handle, 1, stream)
 
     def project(self, z_lo, z_hi, out=None, count=None, stream=None):
         nz, ny, nx = self.shape

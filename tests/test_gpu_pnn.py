@@ -176,6 +176,73 @@ def test_fill_large_accumulators_both_plane_loaders():
         assert not vol.status() & usvol.STATUS_TIMEOUT
 
 
+def _random_accumulators(rng, grid):
+    nx, ny, nz = grid
+    c = np.where(rng.random((nz, ny, nx)) < 0.35, rng.integers(1, 60, (nz, ny, nx)), 0)
+    s = (c * rng.integers(0, 256, (nz, ny, nx))).astype(np.uint64)
+    c = c.astype(np.uint32)
+    return s, c, (c.astype(np.uint64) << np.uint64(32)) | s
+
+
+@pytest.mark.parametrize("grid,spare", [((64, 37, 40), True),    # fused, tensor copies
+                                        ((63, 37, 40), True),    # fused, odd nx
+                                        ((64, 37, 40), False)])  # fill, then reset
+def test_fill_and_clear(grid, spare):
+    """fill_and_clear gives the fill's values and mask, leaves the
+    accumulators zero (every voxel, across several z slabs), and the next
+    sweep on the same volume equals a fresh volume."""
+    import torch
+    import oracle
+    from paper_2412_00058_gb300 import synth, usvol
+    rng = np.random.default_rng(5)
+    vol = usvol.Volume(grid, (0.3, 0.3, 0.3), (0, 0, 0), "pnn", spare=spare)
+    for sweep in range(2):
+        s, c, packed = _random_accumulators(rng, grid)
+        src = torch.from_numpy(packed.view(np.int64)).cuda()
+        usvol.volume_write_accum(vol.handle, src.data_ptr())
+        vol.fill_and_clear()
+        ov, oh = oracle.fill_pnn(s, c)
+        assert np.array_equal(vol.read(usvol.READ_VALUES).cpu().numpy(), ov)
+        assert np.array_equal(vol.read(usvol.READ_MASK).cpu().numpy(), oh)
+        assert not vol.read(usvol.READ_ACCUM).cpu().numpy().any()
+    w = synth.tiny_pnn(n=12, H=48, W=40, grid=grid, band=(10, 20), sweep_mm=2.0, y0_mm=4.0)
+    imgs = torch.from_numpy(w.images).cuda()
+    poses = torch.from_numpy(w.poses).cuda()
+    cal = usvol.calibration_of(w)
+    vol.insert(imgs, poses, cal)
+    vol.fill_and_clear()
+    fresh = usvol.Volume(grid, (0.3, 0.3, 0.3), (0, 0, 0), "pnn")
+    fresh.reset()
+    fresh.insert(imgs, poses, cal)
+    fresh.fill()
+    assert fresh.read(usvol.READ_ACCUM).cpu().numpy().any()
+    for what in (usvol.READ_VALUES, usvol.READ_MASK):
+        assert np.array_equal(vol.read(what).cpu().numpy(), fresh.read(what).cpu().numpy())
+    assert not vol.read(usvol.READ_ACCUM).cpu().numpy().any()
+    assert vol.status() == 0
+
+
+def test_fill_and_clear_trilinear_is_fill_then_reset():
+    import torch
+    from paper_2412_00058_gb300 import usvol
+    grid = (40, 20, 18)
+    rng = np.random.default_rng(8)
+    sw = np.zeros((18, 20, 40, 2), np.float32)
+    m = rng.random((18, 20, 40)) < 0.3
+    sw[m, 1] = rng.random(m.sum()).astype(np.float32) + 0.1
+    sw[m, 0] = sw[m, 1] * rng.integers(0, 256, m.sum())
+    a = usvol.Volume(grid, (0.4,) * 3, (0, 0, 0), "trilinear", spare=True)
+    b = usvol.Volume(grid, (0.4,) * 3, (0, 0, 0), "trilinear")
+    src = torch.from_numpy(sw.view(np.int64)).cuda()
+    for v in (a, b):
+        usvol.volume_write_accum(v.handle, src.data_ptr())
+    a.fill_and_clear()
+    b.fill()
+    for what in (usvol.READ_VALUES, usvol.READ_MASK):
+        assert np.array_equal(a.read(what).cpu().numpy(), b.read(what).cpu().numpy())
+    assert not a.read(usvol.READ_ACCUM).cpu().numpy().any()
+
+
 def test_argument_errors_with_a_live_volume():
     import torch
     from paper_2412_00058_gb300 import synth, usvol
