@@ -55,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="usvol", choices=["usvol", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-tune", action="store_true",
+                   help="keep the default insertion tile shape (skip the autotuner)")
     p.add_argument("--no-variants", action="store_true",
                    help="skip the trilinear convex sweep and pose-gradient timings")
     p.add_argument("--stream-seconds", type=float, default=4.0,
@@ -263,6 +265,7 @@ def measure_variants(dev, reps: int = 5):
     imgs = torch.from_numpy(w.images).to(dev)
     poses = torch.from_numpy(w.poses).to(dev)
     cal = usvol.calibration_of(w)
+    tri_tile, _ = vol.tune(imgs, poses, cal, stream)
     nx, ny, nz = w.grid
     img_out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     cnt = torch.empty((ny, nx), dtype=torch.int16, device=dev)
@@ -286,7 +289,7 @@ def measure_variants(dev, reps: int = 5):
     out["trilinear_convex_sweep"] = {
         "workload": "3000 convex frames 512x512 uint8 (60 deg, 120 mm) -> 400x1700x400 @ 0.4 mm",
         "ms_per_sweep": step, "frames_per_s": w.n / step * 1e3,
-        "insert_ms": ins, "samples_per_s": samples / ins * 1e3}
+        "insert_ms": ins, "samples_per_s": samples / ins * 1e3, "tile": list(tri_tile)}
     del vol, imgs, poses
     torch.cuda.empty_cache()
     w = synth.pose_refine()
@@ -393,6 +396,14 @@ def run_gpu(args):
         if ev is not None:
             ev[3].record(stream)
 
+    # insertion tile shape: the project's autotuner on this sweep's frames
+    tune = None
+    if not args.no_tune:
+        t_t0 = time.perf_counter()
+        tile, tile_ms = vol.tune(imgs, poses, cal, stream)
+        tune = {"tile": list(tile), "default": [128, 64, 8],
+                "insert_ms_first_1024_frames": tile_ms, "candidates": 18,
+                "seconds": time.perf_counter() - t_t0}
     vol.reset(stream)
     for _ in range(max(args.warmup, 3)):
         step()
@@ -552,6 +563,7 @@ def run_gpu(args):
             "streaming": streaming,
             "variants": variants,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches_per_step * K,
+            "autotune": tune,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

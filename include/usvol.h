@@ -78,6 +78,17 @@ typedef struct {
     int32_t nx, ny, nz;
 } usv_grid;
 
+/* Tile shape of the insertion kernels: frames are cut into tiles of
+ * tile_w columns x tile_h rows, and one thread block inserts one tile of
+ * frames_per_cta consecutive frames (no counterpart in the paper; the
+ * results do not depend on it, except for the FP32 summation order of the
+ * trilinear mode).  USV_PNN: tile_w 64, 128 or 256, tile_h 1..1024,
+ * frames_per_cta 1..8; default 128 x 64 x 8.  USV_TRILINEAR: tile_w 256,
+ * tile_h 1..128, frames_per_cta 1..8; default 256 x 64 x 4. */
+typedef struct {
+    int32_t tile_w, tile_h, frames_per_cta;
+} usv_tile_config;
+
 typedef struct {
     double image_to_probe[16]; /* 4x4 row-major, bottom row must be 0 0 0 1 */
     int32_t geom;              /* usv_geom */
@@ -226,6 +237,32 @@ int usv_pose_loss_grad(usv_volume *vol, const void *images_dev, int32_t n, int32
 int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32_t n, int32_t H,
                          int32_t W, const usv_calibration *cal, double *poses_out_dev,
                          void *stream);
+
+/* ------------------------------------------------------------------------
+ * Tile shapes per frame size (no counterpart in the paper).
+ * usv_tune_insert -- the insertion autotuner: inserts the first
+ * min(n, 1024) of the given frames with each candidate tile shape into the
+ * caller's scratch accumulators, times the insertion with CUDA events on
+ * `stream` (the call waits for the stream), and keeps the fastest shape in
+ * the volume for frames of H x W.  The volume's own accumulators are not
+ * touched (its per-frame set-up scratch is).  Candidates: USV_PNN tile_w
+ * {64, 128, 256} x tile_h {32, 64, 128} x frames_per_cta {4, 8};
+ * USV_TRILINEAR tile_h {16, 32, 64, 128} x frames_per_cta {2, 4, 8}.
+ *   scratch_dev    device, 16-byte aligned, >= 8 * nx * ny * nz bytes
+ *   best_out       the chosen shape (may be NULL)
+ *   best_ms_out    its insertion time in ms for the frames tried (may be NULL)
+ * Arguments and errors as usv_insert_frames(), plus USV_ERR_NOMEM for a
+ * short scratch.
+ * usv_set_tile_config sets the shape for frames of H x W (cfg NULL: back to
+ * the default); USV_ERR_RANGE if invalid for the volume's mode, at most 8
+ * frame sizes per volume.  usv_get_tile_config reads the shape in use.
+ * ---------------------------------------------------------------------- */
+int usv_tune_insert(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                    int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                    void *scratch_dev, size_t scratch_bytes, usv_tile_config *best_out,
+                    float *best_ms_out, void *stream);
+int usv_set_tile_config(usv_volume *vol, int32_t H, int32_t W, const usv_tile_config *cfg);
+int usv_get_tile_config(usv_volume *vol, int32_t H, int32_t W, usv_tile_config *out);
 
 /* ------------------------------------------------------------------------
  * usv_fill_holes -- normalisation + hole filling (PNN's second stage; the

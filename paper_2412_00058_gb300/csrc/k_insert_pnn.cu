@@ -6,11 +6,13 @@
 // integer, so the result is exact and independent of execution order.
 //
 // GB300 design:
-//  * one CTA = a tile of up to 128 columns x 64 rows of FPC consecutive
-//    frames; a half-warp covers one 128-pixel row segment, each lane eight
-//    consecutive pixels read with one coalesced 64-bit load (the next row's
-//    load is issued before the current row is processed); the CTA's 16
-//    half-warps take every 16th row.  The near-square tile keeps the box
+//  * one CTA = a tile of TW columns x TH rows of FPC consecutive frames
+//    (default 128 x 64 x 8; TW is 64, 128 or 256, the shape is set per frame
+//    size or chosen by the autotuner); a row segment of TW pixels is TW/8
+//    lanes, each lane eight consecutive pixels read with one coalesced
+//    64-bit load (the next row's load is issued before the current row is
+//    processed).  With the default a half-warp covers one row and the CTA's
+//    16 half-warps take every 16th row.  The near-square tile keeps the box
 //    small: the frames are tilted in plane, and an axis-aligned box around a
 //    tilted 128 x 64 patch holds about 0.09 entries per pixel against 0.13
 //    for a 256 x 32 patch;
@@ -42,13 +44,17 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kPix = 8;              // pixels per lane per row (one 64-bit load)
-constexpr int kTileW = 128;          // columns per tile
-constexpr int kRowLanes = kTileW / kPix;           // lanes per row segment
-constexpr int kWarpRows = 32 / kRowLanes;          // rows per warp per pass
-constexpr int kPassRows = kWarps * kWarpRows;      // rows per CTA per pass
-constexpr int kTileH = 64;           // rows per tile
 constexpr int kSmem = 48 * 1024;     // dynamic shared memory per CTA (the box)
-constexpr int kFpc = 8;              // frames per CTA (<= 8: warp 0 takes 4 corners x 8 frames)
+constexpr int kMaxFpc = 8;           // frames per CTA (warp 0 takes 4 corners x 8 frames)
+
+// Tile geometry for a tile width TW (64, 128 or 256 columns): a row segment
+// of TW pixels is TW/8 lanes, so a warp covers 32/(TW/8) rows per pass.
+template <int TW>
+struct Tile {
+    static constexpr int kRowLanes = TW / kPix;            // lanes per row segment
+    static constexpr int kWarpRows = 32 / kRowLanes;       // rows per warp per pass
+    static constexpr int kPassRows = kWarps * kWarpRows;   // rows per CTA per pass
+};
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
 constexpr int kPackedMaxCount = 1023;
 
@@ -141,12 +147,14 @@ __device__ __forceinline__ void put_group(unsigned *box, unsigned cap, unsigned 
     put_px<0, CHECK, MODE>(box, cap, acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w, npx);
 }
 
-template <bool VEC, bool CHECK, int MODE>
+template <int TW, bool VEC, bool CHECK, int MODE>
 __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1,
                                            int v0, int v1, const long long (&off)[3],
                                            unsigned ex, unsigned ey, unsigned ez, unsigned *box,
                                            unsigned cap, const FrameRec *recs)
 {
+    constexpr int kRowLanes = Tile<TW>::kRowLanes, kWarpRows = Tile<TW>::kWarpRows;
+    constexpr int kPassRows = Tile<TW>::kPassRows;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int u = u0 + kPix * (lane % kRowLanes);
     const int vs = v0 + warp * kWarpRows + lane / kRowLanes;  // this lane's first row
@@ -220,17 +228,17 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
     }
 }
 
-template <bool VEC>
+template <int TW, bool VEC>
 __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
 {
     extern __shared__ unsigned box[];
     __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
-    __shared__ FrameRec s_rec[kFpc];
+    __shared__ FrameRec s_rec[kMaxFpc];
 
     const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
-    const int u0 = tx * kTileW, v0 = ty * a.th;
-    const int u1 = min(a.W, u0 + kTileW), v1 = min(a.H, v0 + a.th);
+    const int u0 = tx * TW, v0 = ty * a.th;
+    const int u1 = min(a.W, u0 + TW), v1 = min(a.H, v0 + a.th);
     const int f0 = blockIdx.y * a.fpc, f1 = min(a.n, f0 + a.fpc);
 
     // the CTA's frame records, copied once into shared memory
@@ -300,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
     if (mode == MODE_DIRECT) {
         // keys are global linear indices into the whole grid
         const long long off[3] = {1LL << 31, 1LL << 31, 1LL << 31};
-        run_frames<VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
+        run_frames<TW, VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
                                            (unsigned)a.ny, (unsigned)a.nz, nullptr, 0, s_rec);
         return;
     }
@@ -318,17 +326,17 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
                               (1LL << 31) - ((long long)s_lo[2] << 32)};
     if (mode == MODE_PACKED) {
         if (s_check)
-            run_frames<VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box, 0,
+            run_frames<TW, VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box, 0,
                                                s_rec);
         else
-            run_frames<VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
+            run_frames<TW, VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
                                                 0, s_rec);
     } else {
         if (s_check)
-            run_frames<VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
+            run_frames<TW, VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
                                               cap, s_rec);
         else
-            run_frames<VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
+            run_frames<TW, VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
                                                cap, s_rec);
     }
     __syncthreads();
@@ -359,11 +367,47 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
 
 }  // namespace
 
+namespace {
+
+template <int TW>
+cudaError_t launch_tw(const PnnArgs &a, dim3 grid, bool vec, cudaStream_t st)
+{
+    // the box plus the CTA's static words exceed the 48 KB default
+    static int attr_device = -1;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn<TW, true>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_insert_pnn<TW, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_device = dev;
+    }
+    if (vec)
+        k_insert_pnn<TW, true><<<grid, kThreads, kSmem, st>>>(a);
+    else
+        k_insert_pnn<TW, false><<<grid, kThreads, kSmem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool pnn_tile_ok(const TileCfg &c)
+{
+    return (c.tile_w == 64 || c.tile_w == 128 || c.tile_w == 256) && c.tile_h >= 1 &&
+           c.tile_h <= 1024 && c.frames_per_cta >= 1 && c.frames_per_cta <= kMaxFpc;
+}
+
 cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H, int W,
-                              cudaStream_t st)
+                              cudaStream_t st, const TileCfg &cfg)
 {
     if (n <= 0)
         return cudaSuccess;
+    if (!pnn_tile_ok(cfg))
+        return cudaErrorInvalidValue;
     PnnArgs a;
     a.img = img;
     a.n = n;
@@ -374,34 +418,20 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;
-    a.th = min(kTileH, H);
-    a.tiles_x = (W + kTileW - 1) / kTileW;
+    a.th = min(cfg.tile_h, H);
+    a.tiles_x = (W + cfg.tile_w - 1) / cfg.tile_w;
     const int tiles_y = (H + a.th - 1) / a.th;
-    a.fpc = kFpc;
+    a.fpc = cfg.frames_per_cta;
     const bool vec = (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
     const long long groups = (n + a.fpc - 1) / a.fpc;
-    if (groups > 65535)
+    if (groups > 65535 || (long long)a.tiles_x * tiles_y > 0x7FFFFFFFLL)
         return cudaErrorInvalidConfiguration;
-    dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
-    // the box plus the CTA's static words exceed the 48 KB default
-    static int attr_device = -1;
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (attr_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn<true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_insert_pnn<false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e != cudaSuccess)
-            return e;
-        attr_device = dev;
+    const dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
+    switch (cfg.tile_w) {
+    case 64: return launch_tw<64>(a, grid, vec, st);
+    case 256: return launch_tw<256>(a, grid, vec, st);
+    default: return launch_tw<128>(a, grid, vec, st);
     }
-    if (vec)
-        k_insert_pnn<true><<<grid, kThreads, kSmem, st>>>(a);
-    else
-        k_insert_pnn<false><<<grid, kThreads, kSmem, st>>>(a);
-    return cudaGetLastError();
 }
 
 }  // namespace usv

@@ -36,11 +36,8 @@ namespace usv {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kCols = 256;                   // columns per tile
-constexpr int kSegs = kThreads / kCols;      // row segments per tile (1)
-constexpr int kRowsPerSeg = 64;
-constexpr int kRows = kSegs * kRowsPerSeg;   // 64 rows per tile
-constexpr int kFpc = 4;                      // frames per CTA
+constexpr int kCols = 256;                   // columns per tile (one per thread)
+constexpr int kMaxFpc = 8;                   // frames per CTA, at most
 constexpr int kBoxBytes = 64 * 1024;
 // Shared FP32 atomic adds measured as a read-retry loop on this part (430
 // instructions per sample, 32 % issue), so the shared box is kept only as
@@ -59,6 +56,8 @@ struct TriArgs {
     int convex;
     double r0, dr;
     int tiles_x;     // column tiles
+    int rows;        // rows per tile
+    int fpc;         // frames per CTA
 };
 
 constexpr long long kOne47 = 1LL << 47;
@@ -235,12 +234,12 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
 __global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
 {
     extern __shared__ float tbox[];  // [kBoxCap] S, then [kBoxCap] W
-    __shared__ FrameRec s_rec[kFpc];
+    __shared__ FrameRec s_rec[kMaxFpc];
     __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
     const int tx = blockIdx.x % a.tiles_x, ty = blockIdx.x / a.tiles_x;
     const int j0 = tx * kCols, j1 = min(a.W, j0 + kCols);
-    const int v0 = ty * kRows, v1 = min(a.H, v0 + kRows);
-    const int f0 = blockIdx.y * kFpc, f1 = min(a.n, f0 + kFpc);
+    const int v0 = ty * a.rows, v1 = min(a.H, v0 + a.rows);
+    const int f0 = blockIdx.y * a.fpc, f1 = min(a.n, f0 + a.fpc);
 
     for (int i = threadIdx.x; i < (f1 - f0) * (int)(sizeof(FrameRec) / 8); i += kThreads)
         reinterpret_cast<unsigned long long *>(s_rec)[i] =
@@ -292,9 +291,8 @@ __global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
     const int mode = s_mode;
     if (mode == 0)
         return;
-    const int j = j0 + (threadIdx.x % kCols);
-    const int seg = threadIdx.x / kCols;
-    const int rv0 = v0 + seg * kRowsPerSeg, rv1 = min(v1, rv0 + kRowsPerSeg);
+    const int j = j0 + threadIdx.x;
+    const int rv0 = v0, rv1 = v1;
     float *bS = tbox, *bW = tbox + kBoxCap;
     if (mode == 2) {
         const int zero[3] = {0, 0, 0};
@@ -333,11 +331,23 @@ __global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
 
 }  // namespace
 
+// A column walks at most tile_h rows from its anchor with steps below 256
+// voxels, so the Q16.47 position stays below 128 * 256 = 2^15 voxels (no
+// overflow of the 64-bit fraction) and drifts by under 2^-41 voxel.
+bool tri_tile_ok(const TileCfg &c)
+{
+    return c.tile_w == kCols && c.tile_h >= 1 && c.tile_h <= 128 && c.frames_per_cta >= 1 &&
+           c.frames_per_cta <= kMaxFpc;
+}
+
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
-                                    int W, int convex, double r0, double dr, cudaStream_t st)
+                                    int W, int convex, double r0, double dr, cudaStream_t st,
+                                    const TileCfg &cfg)
 {
     if (n <= 0)
         return cudaSuccess;
+    if (!tri_tile_ok(cfg))
+        return cudaErrorInvalidValue;
     TriArgs a;
     a.img = img;
     a.is_f32 = is_f32;
@@ -354,8 +364,10 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     a.r0 = r0;
     a.dr = dr;
     a.tiles_x = (W + kCols - 1) / kCols;
-    const int tiles_y = (H + kRows - 1) / kRows;
-    const long long groups = (n + kFpc - 1) / kFpc;
+    a.rows = cfg.tile_h;
+    a.fpc = cfg.frames_per_cta;
+    const int tiles_y = (H + a.rows - 1) / a.rows;
+    const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
     static int attr_device = -1;
@@ -369,7 +381,7 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
         attr_device = dev;
     }
     dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
-    k_insert_trilinear<<<grid, kThreads, kBoxBytes, st>>>(a);
+    k_insert_trilinear<<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);
     return cudaGetLastError();
 }
 

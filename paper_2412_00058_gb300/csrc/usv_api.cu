@@ -1,10 +1,10 @@
 // The C ABI of include/usvol.h: host-side argument checks, the storage
 // layout inside caller-provided device memory, and the launches.  Nothing
 // here allocates device memory; the only host allocation is the handle.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
-
 #include <utility>
 
 #include "usv_internal.cuh"
@@ -202,9 +202,12 @@ int usv_volume_reset(usv_volume *vol, void *stream)
 }
 
 namespace usv {
+// acc_override / cfg_override: insert into other accumulators with a given
+// tile shape (the autotuner); null = the volume's own, tile_for().
 int insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                 int32_t dtype, const double *poses_dev, const usv_calibration *cal,
-                const int32_t *first_rows_dev, void *stream);
+                const int32_t *first_rows_dev, void *stream, void *acc_override = nullptr,
+                const TileCfg *cfg_override = nullptr);
 }
 
 int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
@@ -340,7 +343,8 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
 
 int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
-                     const int32_t *first_rows_dev, void *stream)
+                     const int32_t *first_rows_dev, void *stream, void *acc_override,
+                     const TileCfg *cfg_override)
 {
     if (!vol || !cal || n < 0)
         return USV_ERR_ARG;
@@ -358,7 +362,10 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
         return USV_ERR_ARG;
     if (!usv::affine_ok(cal->image_to_probe))
         return USV_ERR_ARG;
-    Volume &v = *reinterpret_cast<Volume *>(vol);
+    Volume v = *reinterpret_cast<Volume *>(vol);  // a view: acc may be redirected
+    if (acc_override)
+        v.acc = acc_override;
+    const usv::TileCfg cfg = cfg_override ? *cfg_override : usv::tile_for(v, H, W);
     usv::SetupParams sp;
     std::memcpy(sp.K, cal->image_to_probe, sizeof(sp.K));
     for (int a = 0; a < 3; ++a) {
@@ -404,10 +411,11 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
             break;
         const char *img = static_cast<const char *>(images_dev) + (size_t)c0 * frame_bytes;
         if (v.mode == USV_PNN)
-            e = usv::launch_insert_pnn(v, reinterpret_cast<const uint8_t *>(img), nc, H, W, st);
+            e = usv::launch_insert_pnn(v, reinterpret_cast<const uint8_t *>(img), nc, H, W, st,
+                                       cfg);
         else
             e = usv::launch_insert_trilinear(v, img, dtype == USV_F32, nc, H, W, sp.convex,
-                                             cal->r0_mm, cal->dr_mm, st);
+                                             cal->r0_mm, cal->dr_mm, st, cfg);
     }
     if (e == cudaErrorNotSupported)
         return USV_ERR_UNSUPPORTED;
@@ -556,3 +564,162 @@ int usv_status(usv_volume *vol, void *stream)
 }
 
 }  // extern "C"
+
+// ---- tile shapes and the insertion autotuner ----
+
+namespace usv {
+
+TileCfg tile_for(const Volume &v, int H, int W)
+{
+    for (int i = 0; i < v.ntuned; ++i)
+        if (v.tuned[i].H == H && v.tuned[i].W == W)
+            return v.tuned[i].cfg;
+    return v.mode == USV_PNN ? kPnnTileDefault : kTriTileDefault;
+}
+
+namespace {
+
+int find_tuned(const Volume &v, int H, int W)
+{
+    for (int i = 0; i < v.ntuned; ++i)
+        if (v.tuned[i].H == H && v.tuned[i].W == W)
+            return i;
+    return -1;
+}
+
+int store_tuned(Volume &v, int H, int W, const TileCfg &cfg)
+{
+    int i = find_tuned(v, H, W);
+    if (i < 0) {
+        if (v.ntuned == kTunedCap)
+            return USV_ERR_RANGE;
+        i = v.ntuned++;
+    }
+    v.tuned[i] = TunedTile{H, W, cfg};
+    return USV_OK;
+}
+
+// The shapes the autotuner tries, in order (the default first).
+int tune_candidates(int mode, TileCfg *out)
+{
+    int k = 0;
+    if (mode == USV_PNN) {
+        out[k++] = kPnnTileDefault;
+        const int tw[3] = {64, 128, 256}, th[3] = {32, 64, 128}, fpc[2] = {4, 8};
+        for (int a : tw)
+            for (int b : th)
+                for (int c : fpc) {
+                    const TileCfg t{a, b, c};
+                    if (!(a == kPnnTileDefault.tile_w && b == kPnnTileDefault.tile_h &&
+                          c == kPnnTileDefault.frames_per_cta))
+                        out[k++] = t;
+                }
+    } else {
+        out[k++] = kTriTileDefault;
+        const int th[4] = {16, 32, 64, 128}, fpc[3] = {2, 4, 8};
+        for (int b : th)
+            for (int c : fpc) {
+                const TileCfg t{256, b, c};
+                if (!(b == kTriTileDefault.tile_h && c == kTriTileDefault.frames_per_cta))
+                    out[k++] = t;
+            }
+    }
+    return k;
+}
+
+}  // namespace
+
+}  // namespace usv
+
+int usv_set_tile_config(usv_volume *vol, int32_t H, int32_t W, const usv_tile_config *cfg)
+{
+    if (!vol || H < 1 || W < 1)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    const int i = usv::find_tuned(v, H, W);
+    if (!cfg) {
+        if (i >= 0)
+            v.tuned[i] = v.tuned[--v.ntuned];
+        return USV_OK;
+    }
+    if (!(v.mode == USV_PNN ? usv::pnn_tile_ok(*cfg) : usv::tri_tile_ok(*cfg)))
+        return USV_ERR_RANGE;
+    return usv::store_tuned(v, H, W, *cfg);
+}
+
+int usv_get_tile_config(usv_volume *vol, int32_t H, int32_t W, usv_tile_config *out)
+{
+    if (!vol || !out || H < 1 || W < 1)
+        return USV_ERR_ARG;
+    *out = usv::tile_for(*reinterpret_cast<Volume *>(vol), H, W);
+    return USV_OK;
+}
+
+int usv_tune_insert(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
+                    int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                    void *scratch_dev, size_t scratch_bytes, usv_tile_config *best_out,
+                    float *best_ms_out, void *stream)
+{
+    if (!vol || !scratch_dev || n < 1 || (reinterpret_cast<uintptr_t>(scratch_dev) & 15) != 0)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    const size_t acc_bytes = (size_t)v.g.nx * v.g.ny * v.g.nz * 8;
+    if (scratch_bytes < acc_bytes)
+        return USV_ERR_NOMEM;
+    const int nt = n < 1024 ? n : 1024;
+    usv::TileCfg cand[32];
+    const int ncand = usv::tune_candidates(v.mode, cand);
+    usv::DeviceGuard g(v.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (int rc = usv::cuda_rc(cudaEventCreate(&e0)))
+        return rc;
+    if (int rc = usv::cuda_rc(cudaEventCreate(&e1))) {
+        cudaEventDestroy(e0);
+        return rc;
+    }
+    int rc = USV_OK;
+    usv::TileCfg best = cand[0];
+    float best_ms = 0.0f;
+    bool have = false;
+    for (int c = 0; c < ncand && rc == USV_OK; ++c) {
+        float t[3];
+        for (int rep = 0; rep < 4 && rc == USV_OK; ++rep) {  // rep 0 warms up
+            rc = usv::cuda_rc(usv::launch_zero(scratch_dev, acc_bytes, v.num_sms, st));
+            if (rc == USV_OK)
+                rc = usv::cuda_rc(cudaEventRecord(e0, st));
+            if (rc == USV_OK)
+                rc = usv::insert_impl(vol, images_dev, nt, H, W, dtype, poses_dev, cal, nullptr,
+                                      stream, scratch_dev, &cand[c]);
+            if (rc == USV_OK)
+                rc = usv::cuda_rc(cudaEventRecord(e1, st));
+            if (rc == USV_OK)
+                rc = usv::cuda_rc(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            if (rc == USV_OK)
+                rc = usv::cuda_rc(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0)
+                t[rep - 1] = ms;
+        }
+        if (rc != USV_OK)
+            break;
+        const float med = std::max(std::min(t[0], t[1]), std::min(std::max(t[0], t[1]), t[2]));
+        if (!have || med < best_ms) {
+            best = cand[c];
+            best_ms = med;
+            have = true;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != USV_OK)
+        return rc;
+    rc = usv::store_tuned(v, H, W, best);
+    if (rc != USV_OK)
+        return rc;
+    if (best_out)
+        *best_out = best;
+    if (best_ms_out)
+        *best_ms_out = best_ms;
+    return USV_OK;
+}

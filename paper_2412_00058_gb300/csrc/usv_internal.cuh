@@ -22,6 +22,19 @@ struct FrameRec {
 static_assert(sizeof(FrameRec) == 160, "FrameRec layout");
 
 // Host-side handle behind usv_volume*.
+// Insertion tile shape (the public usv_tile_config).
+using TileCfg = usv_tile_config;
+// Defaults, from the whole-spine profiles: PNN 128 x 64 pixels x 8 frames,
+// trilinear 256 columns x 64 rows x 4 frames.
+constexpr TileCfg kPnnTileDefault = {128, 64, 8};
+constexpr TileCfg kTriTileDefault = {256, 64, 4};
+constexpr int kTunedCap = 8;  // frame sizes (H, W) with a chosen tile per volume
+
+struct TunedTile {
+    int H, W;
+    TileCfg cfg;
+};
+
 struct Volume {
     usv_grid g;
     double spacing[3];
@@ -39,7 +52,15 @@ struct Volume {
     uint32_t *status;   // one word of USV_STATUS_* bits
     int num_sms;
     int device;
+    TunedTile tuned[kTunedCap];  // tile shapes set or tuned per frame size
+    int ntuned;
 };
+
+// The tile for frames of H x W in this volume: a tuned or set one, else the
+// mode's default.
+TileCfg tile_for(const Volume &v, int H, int W);
+bool pnn_tile_ok(const TileCfg &c);
+bool tri_tile_ok(const TileCfg &c);
 
 constexpr int kRecCap = 4096;      // frames per set-up + insert launch pair
 constexpr int kBeamCap = 32768;    // max W
@@ -73,9 +94,10 @@ cudaError_t launch_bone_rows_alg2(const uint8_t *img, int n, int H, int W, int f
                                   int window, int margin, int32_t *bone_rows, int32_t *first_rows,
                                   cudaStream_t st);
 cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H, int W,
-                              cudaStream_t st);
+                              cudaStream_t st, const TileCfg &cfg = kPnnTileDefault);
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
-                                    int W, int convex, double r0, double dr, cudaStream_t st);
+                                    int W, int convex, double r0, double dr, cudaStream_t st,
+                                    const TileCfg &cfg = kTriTileDefault);
 // fill / project a region: voxels [lo, hi) (clipped to the grid; the fill
 // needs lo[0] a multiple of 32), columns [rlo, rhi)
 cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st,

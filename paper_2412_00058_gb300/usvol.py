@@ -37,7 +37,8 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_abi_version", "usv_insert_pnn_noalloc", "usv_fill_holes_region",
            "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
            "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta",
-           "usv_fill_holes_and_clear")
+           "usv_fill_holes_and_clear", "usv_tune_insert", "usv_set_tile_config",
+           "usv_get_tile_config")
 
 
 class UsvError(RuntimeError):
@@ -51,6 +52,15 @@ class UsvError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class TileConfig(ctypes.Structure):
+    """Insertion tile shape (usv_tile_config)."""
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("frames_per_cta", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.tile_w, self.tile_h, self.frames_per_cta)
 
 
 class Calibration(ctypes.Structure):
@@ -245,6 +255,34 @@ def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
                                 ctypes.c_void_p(_stream_ptr(stream))), "usv_fill_holes")
 
 
+def tune_insert(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
+                poses_ptr: int, cal: Calibration, scratch_ptr: int, scratch_bytes: int,
+                stream=None):
+    """Run the insertion autotuner; returns (TileConfig, ms)."""
+    best = TileConfig()
+    ms = ctypes.c_float()
+    _check(lib().usv_tune_insert(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H, W,
+                                 dtype, ctypes.c_void_p(poses_ptr), ctypes.byref(cal),
+                                 ctypes.c_void_p(scratch_ptr), ctypes.c_size_t(scratch_bytes),
+                                 ctypes.byref(best), ctypes.byref(ms),
+                                 ctypes.c_void_p(_stream_ptr(stream))), "usv_tune_insert")
+    return best, ms.value
+
+
+def set_tile_config(handle: int, H: int, W: int, cfg) -> None:
+    c = None if cfg is None else TileConfig(*cfg)
+    _check(lib().usv_set_tile_config(ctypes.c_void_p(handle), H, W,
+                                     ctypes.byref(c) if c is not None else None),
+           "usv_set_tile_config")
+
+
+def get_tile_config(handle: int, H: int, W: int) -> tuple:
+    out = TileConfig()
+    _check(lib().usv_get_tile_config(ctypes.c_void_p(handle), H, W, ctypes.byref(out)),
+           "usv_get_tile_config")
+    return out.as_tuple()
+
+
 def fill_holes_and_clear(handle: int, radius: int = 1, stream=None) -> None:
     _check(lib().usv_fill_holes_and_clear(ctypes.c_void_p(handle), radius,
                                           ctypes.c_void_p(_stream_ptr(stream))),
@@ -340,6 +378,24 @@ class Volume:
         if dt == F32:
             assert images.dtype == torch.float32
         insert_frames(self.handle, images.data_ptr(), n, H, W, dt, poses.data_ptr(), cal, stream)
+
+    def tune(self, images: torch.Tensor, poses: torch.Tensor, cal: Calibration, stream=None):
+        """Autotune the insertion tile shape for these frames (scratch
+        accumulators from torch); the choice is kept for their frame size.
+        Returns ((tile_w, tile_h, frames_per_cta), ms)."""
+        n, H, W = images.shape
+        dt = U8 if images.dtype == torch.uint8 else F32
+        nx, ny, nz = self.grid
+        scratch = torch.empty(nx * ny * nz, dtype=torch.int64, device=self.storage.device)
+        best, ms = tune_insert(self.handle, images.data_ptr(), n, H, W, dt, poses.data_ptr(), cal,
+                               scratch.data_ptr(), scratch.numel() * 8, stream)
+        return best.as_tuple(), ms
+
+    def set_tile(self, H: int, W: int, cfg) -> None:
+        set_tile_config(self.handle, H, W, cfg)
+
+    def get_tile(self, H: int, W: int) -> tuple:
+        return get_tile_config(self.handle, H, W)
 
     def fill(self, stream=None):
         fill_holes(self.handle, 1, stream)
