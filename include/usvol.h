@@ -239,6 +239,33 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
                          void *stream);
 
 /* ------------------------------------------------------------------------
+ * usv_insert_frames_multi -- several (volume, batch of frames) jobs in one
+ * go: the batches of concurrent scan sessions, each of its own size (the
+ * paper processes the newly acquired frames of each scan incrementally,
+ * Sec. II.C; batching sessions together has no counterpart there).  The
+ * result in every volume is bit-identical to usv_insert_frames() of its job.
+ * Two launches in all: one frame set-up over all jobs and one persistent
+ * insertion kernel whose thread blocks walk the jobs' tiles of frames.
+ * Every job: a USV_PNN volume, USV_U8 frames, a USV_LINEAR calibration,
+ * 0 <= n <= 4096 frames; the arguments of a job mean what they mean for
+ * usv_insert_frames().  All volumes on one device, each in at most one job,
+ * at most 32 jobs (USV_ERR_RANGE beyond; USV_ERR_ARG for a repeated volume
+ * or volumes on different devices; USV_ERR_UNSUPPORTED for other modes or
+ * geometries).  A volume's tile shape (usv_set_tile_config, usv_tune_insert)
+ * applies when its tile_w is 128, else 128 x 64 x 8.
+ * ---------------------------------------------------------------------- */
+typedef struct {
+    usv_volume *vol;
+    const void *images_dev;  /* [n][H][W] uint8 */
+    int32_t n, H, W;
+    int32_t dtype;           /* USV_U8 */
+    const double *poses_dev; /* [n][16] row-major probe->world, mm */
+    const usv_calibration *cal;
+} usv_insert_job;
+
+int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *stream);
+
+/* ------------------------------------------------------------------------
  * Tile shapes per frame size (no counterpart in the paper).
  * usv_tune_insert -- the insertion autotuner: inserts the first
  * min(n, 1024) of the given frames with each candidate tile shape into the

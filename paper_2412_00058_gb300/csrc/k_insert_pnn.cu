@@ -228,18 +228,20 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
     }
 }
 
+// One CTA's work: tile `tile` of the frame group `group` (frames
+// group*fpc ..).  Every thread of the CTA calls it with the same arguments;
+// it leaves shared memory to be reused only after a barrier.
 template <int TW, bool VEC>
-__global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
+__device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int group)
 {
     extern __shared__ unsigned box[];
     __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
     __shared__ FrameRec s_rec[kMaxFpc];
 
-    const int tile = blockIdx.x;
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int u0 = tx * TW, v0 = ty * a.th;
     const int u1 = min(a.W, u0 + TW), v1 = min(a.H, v0 + a.th);
-    const int f0 = blockIdx.y * a.fpc, f1 = min(a.n, f0 + a.fpc);
+    const int f0 = group * a.fpc, f1 = min(a.n, f0 + a.fpc);
 
     // the CTA's frame records, copied once into shared memory
     for (int i = threadIdx.x; i < (f1 - f0) * (int)(sizeof(FrameRec) / 8); i += kThreads)
@@ -365,6 +367,41 @@ __global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
     }
 }
 
+template <int TW, bool VEC>
+__global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
+{
+    insert_tile<TW, VEC>(a, blockIdx.x, blockIdx.y);
+}
+
+// Several (volume, frames) jobs in one persistent launch: the work items
+// are all jobs' (frame group, tile) pairs, job after job; each CTA takes
+// items blockIdx.x, blockIdx.x + gridDim.x, ... so consecutive items (tiles
+// of one frame group) run side by side.
+struct PnnJobs {
+    int njobs;
+    long long begin[kMaxJobs + 1];  // prefix sums of the jobs' item counts
+    int tiles[kMaxJobs];            // tiles per frame group
+    int vec[kMaxJobs];
+    PnnArgs args[kMaxJobs];
+};
+
+__global__ void __launch_bounds__(kThreads) k_insert_pnn_multi(const __grid_constant__ PnnJobs J)
+{
+    const long long total = J.begin[J.njobs];
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        int j = 0;
+        while (item >= J.begin[j + 1])
+            ++j;
+        const long long local = item - J.begin[j];
+        const int tile = (int)(local % J.tiles[j]), group = (int)(local / J.tiles[j]);
+        if (J.vec[j])
+            insert_tile<128, true>(J.args[j], tile, group);
+        else
+            insert_tile<128, false>(J.args[j], tile, group);
+        __syncthreads();  // the next item reuses the box and the CTA's words
+    }
+}
+
 }  // namespace
 
 namespace {
@@ -399,6 +436,76 @@ bool pnn_tile_ok(const TileCfg &c)
 {
     return (c.tile_w == 64 || c.tile_w == 128 || c.tile_w == 256) && c.tile_h >= 1 &&
            c.tile_h <= 1024 && c.frames_per_cta >= 1 && c.frames_per_cta <= kMaxFpc;
+}
+
+namespace {
+
+PnnArgs make_args(const Volume &v, const uint8_t *img, int n, int H, int W, const TileCfg &cfg)
+{
+    PnnArgs a;
+    a.img = img;
+    a.n = n;
+    a.H = H;
+    a.W = W;
+    a.rec = v.rec;
+    a.acc = reinterpret_cast<unsigned long long *>(v.acc);
+    a.nx = v.g.nx;
+    a.ny = v.g.ny;
+    a.nz = v.g.nz;
+    a.th = min(cfg.tile_h, H);
+    a.tiles_x = (W + cfg.tile_w - 1) / cfg.tile_w;
+    a.fpc = cfg.frames_per_cta;
+    return a;
+}
+
+bool vec_ok(const uint8_t *img, int W)
+{
+    return (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
+}
+
+}  // namespace
+
+cudaError_t launch_insert_pnn_multi(const InsertJob *jobs, int njobs, int num_sms,
+                                    cudaStream_t st)
+{
+    if (njobs < 0 || njobs > kMaxJobs)
+        return cudaErrorInvalidValue;
+    PnnJobs J;
+    J.njobs = njobs;
+    J.begin[0] = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const InsertJob &b = jobs[j];
+        if (b.cfg.tile_w != 128 || !pnn_tile_ok(b.cfg))
+            return cudaErrorInvalidValue;
+        J.args[j] = make_args(*b.v, b.img, b.n, b.H, b.W, b.cfg);
+        const int tiles_y = (b.H + J.args[j].th - 1) / J.args[j].th;
+        J.tiles[j] = J.args[j].tiles_x * tiles_y;
+        J.vec[j] = vec_ok(b.img, b.W) ? 1 : 0;
+        const long long groups = b.n > 0 ? (b.n + b.cfg.frames_per_cta - 1) / b.cfg.frames_per_cta
+                                         : 0;
+        J.begin[j + 1] = J.begin[j] + groups * J.tiles[j];
+    }
+    const long long total = J.begin[njobs];
+    if (total == 0)
+        return cudaSuccess;
+    static int attr_device = -1, per_sm = 1;
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (attr_device != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn_multi,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert_pnn_multi,
+                                                              kThreads, kSmem);
+        if (e != cudaSuccess)
+            return e;
+        per_sm = per_sm < 1 ? 1 : per_sm;
+        attr_device = dev;
+    }
+    const long long resident = (long long)num_sms * per_sm;
+    const unsigned grid = (unsigned)(total < resident ? total : resident);
+    k_insert_pnn_multi<<<grid, kThreads, kSmem, st>>>(J);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H, int W,

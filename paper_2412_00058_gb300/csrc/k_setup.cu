@@ -57,13 +57,10 @@ __device__ int pixels_per_voxel_bound(const double *d)
     return n >= 1048576.0 ? (1 << 20) : (int)n;
 }
 
-__global__ void k_frame_setup(const double *__restrict__ poses, int n, SetupParams sp,
-                              FrameRec *__restrict__ rec, uint32_t *status)
+// Frame f's record from its pose P (16 FP64, row-major).
+__device__ void setup_frame(const double *__restrict__ P, int f, const SetupParams &sp,
+                            FrameRec *__restrict__ rec, uint32_t *status)
 {
-    const int f = blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= n)
-        return;
-    const double *P = poses + (size_t)f * 16;
     double p[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i)
@@ -104,6 +101,29 @@ __global__ void k_frame_setup(const double *__restrict__ poses, int n, SetupPara
         atomicOr(status, USV_STATUS_BAD_POSE);
 }
 
+__global__ void k_frame_setup(const double *__restrict__ poses, int n, SetupParams sp,
+                              FrameRec *__restrict__ rec, uint32_t *status)
+{
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f < n)
+        setup_frame(poses + (size_t)f * 16, f, sp, rec, status);
+}
+
+// All jobs' frames in one launch: thread t takes frame t - begin[j] of the
+// job j with begin[j] <= t < begin[j + 1].
+__global__ void k_frame_setup_multi(const __grid_constant__ SetupJobs J)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= J.begin[J.njobs])
+        return;
+    int j = 0;
+    while (t >= J.begin[j + 1])
+        ++j;
+    const int f = t - J.begin[j];
+    const SetupJob &b = J.job[j];
+    setup_frame(b.poses + (size_t)f * 16, f, b.sp, b.rec, b.status);
+}
+
 // Beam directions of a convex probe: theta_j = -sector/2 + j*sector/(W-1)
 // (beams spread evenly over the sector, both ends included).
 __global__ void k_beam_setup(double2 *beams, int W, double half_rad, double step_rad)
@@ -125,6 +145,15 @@ cudaError_t launch_frame_setup(const double *poses, int n, const SetupParams &sp
     if (n <= 0)
         return cudaSuccess;
     k_frame_setup<<<(n + 127) / 128, 128, 0, st>>>(poses, n, sp, rec, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_frame_setup_multi(const SetupJobs &jobs, cudaStream_t st)
+{
+    const int total = jobs.begin[jobs.njobs];
+    if (total <= 0)
+        return cudaSuccess;
+    k_frame_setup_multi<<<(total + 127) / 128, 128, 0, st>>>(jobs);
     return cudaGetLastError();
 }
 

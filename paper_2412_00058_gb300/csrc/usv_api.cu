@@ -723,3 +723,76 @@ int usv_tune_insert(usv_volume *vol, const void *images_dev, int32_t n, int32_t 
         *best_ms_out = best_ms;
     return USV_OK;
 }
+
+// ---- several (volume, frames) jobs in one launch pair ----
+
+int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *stream)
+{
+    if (njobs < 0 || (njobs > 0 && !jobs))
+        return USV_ERR_ARG;
+    if (njobs > usv::kMaxJobs)
+        return USV_ERR_RANGE;
+    usv::SetupJobs sj;
+    usv::InsertJob ij[usv::kMaxJobs];
+    const Volume *vols[usv::kMaxJobs];
+    int m = 0, device = -1, num_sms = 0;
+    sj.begin[0] = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const usv_insert_job &b = jobs[j];
+        if (!b.vol || !b.cal || b.n < 0)
+            return USV_ERR_ARG;
+        const Volume &v = *reinterpret_cast<const Volume *>(b.vol);
+        for (int k = 0; k < m; ++k)
+            if (vols[k] == &v)
+                return USV_ERR_ARG;  // one job per volume (its set-up scratch)
+        if (device >= 0 && v.device != device)
+            return USV_ERR_ARG;
+        if (v.mode != USV_PNN || b.dtype != USV_U8 || b.cal->geom != USV_LINEAR)
+            return b.dtype != USV_U8 && b.dtype != USV_F32 ? USV_ERR_ARG : USV_ERR_UNSUPPORTED;
+        if (b.n > usv::kRecCap)
+            return USV_ERR_RANGE;
+        if (b.n == 0)
+            continue;
+        if (!b.images_dev || !b.poses_dev || (reinterpret_cast<uintptr_t>(b.poses_dev) & 7) != 0)
+            return USV_ERR_ARG;
+        if (b.H < 1 || b.W < 1)
+            return USV_ERR_ARG;
+        if (b.H > usv::kMaxDim || b.W > usv::kMaxDim)
+            return USV_ERR_RANGE;
+        if (!usv::affine_ok(b.cal->image_to_probe))
+            return USV_ERR_ARG;
+        if (!(std::isfinite(b.cal->sx_mm) && std::isfinite(b.cal->sy_mm) && b.cal->sx_mm > 0.0 &&
+              b.cal->sy_mm > 0.0))
+            return USV_ERR_ARG;
+        device = v.device;
+        num_sms = v.num_sms;
+        usv::SetupJob &s = sj.job[m];
+        s.poses = b.poses_dev;
+        std::memcpy(s.sp.K, b.cal->image_to_probe, sizeof(s.sp.K));
+        for (int a = 0; a < 3; ++a) {
+            s.sp.s[a] = v.spacing[a];
+            s.sp.o[a] = v.origin[a];
+        }
+        s.sp.sx = b.cal->sx_mm;
+        s.sp.sy = b.cal->sy_mm;
+        s.sp.convex = 0;
+        s.sp.first_rows = nullptr;
+        s.rec = v.rec;
+        s.status = v.status;
+        sj.begin[m + 1] = sj.begin[m] + b.n;
+        usv::TileCfg cfg = usv::tile_for(v, b.H, b.W);
+        if (cfg.tile_w != 128)
+            cfg = usv::kPnnTileDefault;
+        ij[m] = usv::InsertJob{&v, static_cast<const uint8_t *>(b.images_dev), b.n, b.H, b.W, cfg};
+        vols[m++] = &v;
+    }
+    sj.njobs = m;
+    if (m == 0)
+        return USV_OK;
+    usv::DeviceGuard g(device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = usv::launch_frame_setup_multi(sj, st);
+    if (e == cudaSuccess)
+        e = usv::launch_insert_pnn_multi(ij, m, num_sms, st);
+    return usv::cuda_rc(e);
+}

@@ -80,10 +80,33 @@ struct SetupParams {
     const int32_t *first_rows;  // per-frame first inserted row, or null (all rows)
 };
 
+// Several (volume, batch of frames) jobs in one launch (usv_insert_frames_multi).
+constexpr int kMaxJobs = 32;
+struct SetupJob {
+    const double *poses;
+    SetupParams sp;
+    FrameRec *rec;
+    uint32_t *status;
+};
+struct SetupJobs {
+    int njobs;
+    int begin[kMaxJobs + 1];  // prefix sums of the jobs' frame counts
+    SetupJob job[kMaxJobs];
+};
+struct InsertJob {
+    const Volume *v;
+    const uint8_t *img;
+    int n, H, W;
+    TileCfg cfg;  // tile_w must be 128
+};
+
 // ---- launchers (each in its own translation unit) ----
 cudaError_t launch_frame_setup(const double *poses, int n, const SetupParams &sp, FrameRec *rec,
                                uint32_t *status, cudaStream_t st);
 cudaError_t launch_beam_setup(double2 *beams, int W, double sector_deg, cudaStream_t st);
+cudaError_t launch_frame_setup_multi(const SetupJobs &jobs, cudaStream_t st);
+cudaError_t launch_insert_pnn_multi(const InsertJob *jobs, int njobs, int num_sms,
+                                    cudaStream_t st);
 struct Alg1Params {
     double K[16];
     double k, d_mm, half_l_mm, dir[3], p1[3], row_mm;

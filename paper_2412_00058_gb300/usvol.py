@@ -38,7 +38,7 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
            "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta",
            "usv_fill_holes_and_clear", "usv_tune_insert", "usv_set_tile_config",
-           "usv_get_tile_config")
+           "usv_get_tile_config", "usv_insert_frames_multi")
 
 
 class UsvError(RuntimeError):
@@ -61,6 +61,14 @@ class TileConfig(ctypes.Structure):
 
     def as_tuple(self):
         return (self.tile_w, self.tile_h, self.frames_per_cta)
+
+
+class InsertJob(ctypes.Structure):
+    """One (volume, batch of frames) job of usv_insert_frames_multi."""
+    _fields_ = [("vol", ctypes.c_void_p), ("images_dev", ctypes.c_void_p),
+                ("n", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("dtype", ctypes.c_int32), ("poses_dev", ctypes.c_void_p),
+                ("cal", ctypes.c_void_p)]
 
 
 class Calibration(ctypes.Structure):
@@ -253,6 +261,20 @@ def apply_pose_delta(poses_ptr: int, delta_ptr: int, n: int, H: int, W: int, cal
 def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
     _check(lib().usv_fill_holes(ctypes.c_void_p(handle), radius,
                                 ctypes.c_void_p(_stream_ptr(stream))), "usv_fill_holes")
+
+
+def insert_frames_multi(jobs, stream=None) -> None:
+    """jobs: sequence of (Volume, images [n,H,W] u8, poses [n,4,4] f64, Calibration)."""
+    arr = (InsertJob * max(len(jobs), 1))()
+    keep = []
+    for k, (vol, images, poses, cal) in enumerate(jobs):
+        assert images.is_cuda and poses.is_cuda and images.is_contiguous() and poses.is_contiguous()
+        n, H, W = images.shape
+        keep.append(cal)
+        arr[k] = InsertJob(vol.handle, images.data_ptr(), n, H, W, U8, poses.data_ptr(),
+                           ctypes.cast(ctypes.pointer(cal), ctypes.c_void_p))
+    _check(lib().usv_insert_frames_multi(arr, len(jobs), ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_insert_frames_multi")
 
 
 def tune_insert(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
