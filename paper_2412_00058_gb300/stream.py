@@ -17,6 +17,14 @@ moment its refreshed projection is complete on the device, observed from
 the host.  Sessions are admitted only while their device memory fits a
 budget; every volume stays resident.
 
+Two dispatch modes.  Per-session streams: each burst is enqueued on its
+session's stream as it arrives.  Batched: one engine stream; whenever it
+dispatches, it takes every session's oldest waiting burst, inserts all the
+nearest-neighbour ones with one usv_insert_frames_multi call (one set-up and
+one persistent insertion launch over all volumes), then refreshes each
+session's region.  Either mode can also replay the scans as fast as the GPU
+takes them (no real-time pacing) to measure serving throughput.
+
 All GPU work is the library's kernels (through the C ABI); this module only
 schedules.
 """
@@ -126,19 +134,26 @@ class Session:
             yield t0 + (f + b) / self.fps, f, b
             f += b
 
-    def dispatch(self, f0: int, b: int):
-        """Enqueue one burst on the session's stream; returns its done-event."""
+    def stage(self, f0: int, b: int, st):
+        """Host->device copy of burst [f0, f0 + b) into the staging buffers."""
+        self.d_imgs[:b].copy_(self.h_imgs[f0:f0 + b], non_blocking=True)
+        self.d_poses[:b].copy_(self.h_poses[f0:f0 + b], non_blocking=True)
+
+    def refresh(self, f0: int, b: int, st):
+        """Fill + projection of the region burst [f0, f0 + b) touched."""
         w = self.w
         lo, hi = frames_voxel_box(w, w.poses[f0:f0 + b])
+        usvol.fill_holes_region(self.vol.handle, lo, hi, 1, st)
+        usvol.project_depth_band_region(self.vol.handle, w.band[0], w.band[1], lo[:2], hi[:2],
+                                        self.out.data_ptr(), self.cnt.data_ptr(), st)
+
+    def dispatch(self, f0: int, b: int):
+        """Enqueue one burst on the session's stream; returns its done-event."""
         st = self.stream
         with torch.cuda.stream(st):
-            self.d_imgs[:b].copy_(self.h_imgs[f0:f0 + b], non_blocking=True)
-            self.d_poses[:b].copy_(self.h_poses[f0:f0 + b], non_blocking=True)
+            self.stage(f0, b, st)
             self.vol.insert(self.d_imgs[:b], self.d_poses[:b], self.cal, st)
-            usvol.fill_holes_region(self.vol.handle, lo, hi, 1, st)
-            usvol.project_depth_band_region(self.vol.handle, w.band[0], w.band[1], lo[:2],
-                                            hi[:2], self.out.data_ptr(), self.cnt.data_ptr(),
-                                            st)
+            self.refresh(f0, b, st)
             ev = torch.cuda.Event()
             ev.record(st)
         return ev
@@ -167,18 +182,48 @@ class Scheduler:
         self.sessions.append(s)
         return s
 
-    def run(self, seconds: float | None = None):
-        """Stream every session's frames at its frame rate (for at most
-        `seconds` of scan time); returns the per-session stats."""
-        torch.cuda.synchronize(self.device)
-        t0 = time.perf_counter() + 0.05
+    def _events(self, t0: float, seconds, realtime: bool):
         events = []
         for si, s in enumerate(self.sessions):
             for t, f0, b in s.arrivals(t0):
                 if seconds is not None and t - t0 > seconds:
                     break
-                events.append((t, si, f0, b))
-        events.sort()
+                events.append((t if realtime else t0, si, f0, b))
+        events.sort(key=lambda e: (e[0], e[2], e[1]))
+        return events
+
+    def dispatch_batch(self, bursts, st):
+        """One engine dispatch: bursts = [(session index, f0, b)], at most one
+        per session.  Returns the done-event."""
+        with torch.cuda.stream(st):
+            for si, f0, b in bursts:
+                self.sessions[si].stage(f0, b, st)
+            pnn = [(si, b) for si, _, b in bursts if self.sessions[si].w.mode == "pnn"]
+            if pnn:
+                usvol.insert_frames_multi(
+                    [(self.sessions[si].vol, self.sessions[si].d_imgs[:b],
+                      self.sessions[si].d_poses[:b], self.sessions[si].cal) for si, b in pnn], st)
+            for si, f0, b in bursts:
+                s = self.sessions[si]
+                if s.w.mode != "pnn":
+                    s.vol.insert(s.d_imgs[:b], s.d_poses[:b], s.cal, st)
+            for si, f0, b in bursts:
+                self.sessions[si].refresh(f0, b, st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return ev
+
+    def run(self, seconds: float | None = None, batched: bool = False, realtime: bool = True):
+        """Stream every session's frames at its frame rate (for at most
+        `seconds` of scan time); returns the per-session stats.  batched:
+        one engine stream with multi-volume insertion; realtime=False: every
+        burst is available at once and the GPU takes them as fast as it can
+        (latencies then measure queueing, use wall_s for throughput)."""
+        if batched:
+            return self._run_batched(seconds, realtime)
+        torch.cuda.synchronize(self.device)
+        t0 = time.perf_counter() + 0.05
+        events = self._events(t0, seconds, realtime)
         queues = [[] for _ in self.sessions]
         conds = [threading.Condition() for _ in self.sessions]
         done = [False] * len(self.sessions)
@@ -216,6 +261,64 @@ class Scheduler:
                 conds[si].notify()
         for th in threads:
             th.join()
+        self.wall_s = time.perf_counter() - t0
+        return [s.stats for s in self.sessions]
+
+    def _run_batched(self, seconds, realtime: bool):
+        torch.cuda.synchronize(self.device)
+        engine = torch.cuda.Stream(self.device)
+        t0 = time.perf_counter() + 0.05
+        pending = self._events(t0, seconds, realtime)
+        queue, cond, state = [], threading.Condition(), {"done": False}
+        self.dispatches = 0
+
+        def watch():
+            while True:
+                with cond:
+                    while not queue and not state["done"]:
+                        cond.wait()
+                    if not queue:
+                        return
+                    ev, members = queue.pop(0)
+                ev.synchronize()
+                now = time.perf_counter()
+                for si, t_arr, b in members:
+                    st = self.sessions[si].stats
+                    st.latencies_ms.extend([(now - t_arr) * 1e3] * b)
+                    st.frames += b
+                    st.bursts += 1
+
+        th = threading.Thread(target=watch, daemon=True)
+        th.start()
+        i = 0
+        while i < len(pending):
+            delay = pending[i][0] - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            now = time.perf_counter()
+            # every session's oldest burst that has arrived (one per session:
+            # its staging buffers hold one burst)
+            take, seen, rest = [], set(), []
+            for e in pending[i:]:
+                if e[0] > now:
+                    rest.append(e)
+                elif e[1] in seen:
+                    rest.append(e)
+                else:
+                    seen.add(e[1])
+                    take.append(e)
+            ev = self.dispatch_batch([(si, f0, b) for _, si, f0, b in take], engine)
+            self.dispatches += 1
+            with cond:
+                queue.append((ev, [(si, t, b) for t, si, f0, b in take]))
+                cond.notify()
+            pending = sorted(rest, key=lambda e: (e[0], e[2], e[1]))
+            i = 0
+        with cond:
+            state["done"] = True
+            cond.notify()
+        th.join()
+        self.wall_s = time.perf_counter() - t0
         return [s.stats for s in self.sessions]
 
 

@@ -32,7 +32,11 @@ def test_frames_voxel_box_contains_every_pixel_voxel():
 
 
 @pytest.mark.gpu
-def test_streamed_scan_equals_one_shot_and_full_refresh():
+@pytest.mark.parametrize("batched,realtime", [(False, True), (True, True), (True, False)])
+def test_streamed_scan_equals_one_shot_and_full_refresh(batched, realtime):
+    """Per-session streams, and the batched engine (one multi-volume
+    insertion per dispatch over two nearest-neighbour sessions and a
+    trilinear one), paced in real time or replayed at once."""
     import torch
     from helpers import build_library
     from paper_2412_00058_gb300 import stream, synth, usvol
@@ -44,14 +48,19 @@ def test_streamed_scan_equals_one_shot_and_full_refresh():
     w2 = synth.convex_fan(n=40, H=160, W=96, depth_mm=40.0, r0_mm=20.0, grid=(180, 80, 150),
                           spacing=0.4, band=(40, 70), sweep_mm=12.0, sway_mm=3.0,
                           y_start_mm=6.0)
+    w3 = synth.tiny_pnn(n=50)
     s1 = sched.admit("pnn", w1, 120.0, seed=1)
     s2 = sched.admit("tri", w2, 60.0, seed=2)
-    stats = sched.run()
+    s3 = sched.admit("tiny", w3, 60.0, seed=3)
+    stats = sched.run(batched=batched, realtime=realtime)
     torch.cuda.synchronize()
-    assert stats[0].frames == w1.n and stats[1].frames == w2.n
+    assert [st.frames for st in stats] == [w1.n, w2.n, w3.n]
     summ = stream.summary(stats)
-    assert summ["p99_ms"] < 100.0
-    for s, w in ((s1, w1), (s2, w2)):
+    if realtime:
+        assert summ["p99_ms"] < 100.0
+    if batched:
+        assert sched.dispatches <= sum(st.bursts for st in stats)
+    for s, w in ((s1, w1), (s2, w2), (s3, w3)):
         ref = usvol.Volume(w.grid, w.spacing, w.origin, w.mode)
         ref.reset()
         ref.insert(torch.from_numpy(w.images).cuda(), torch.from_numpy(w.poses).cuda(),
