@@ -55,6 +55,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="usvol", choices=["usvol", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-graph", action="store_true",
+                   help="skip the CUDA-graph replay of the step")
     p.add_argument("--no-tune", action="store_true",
                    help="keep the default insertion tile shape (skip the autotuner)")
     p.add_argument("--no-variants", action="store_true",
@@ -450,6 +452,34 @@ def run_gpu(args):
     value = frames / (total_ms / 1e3)
     vupd = hits * world * K / (total_ms / 1e3)
 
+    # ---- the same step replayed from a captured CUDA graph (two steps per
+    # graph: the accumulator sets swap at every step)
+    graph = None
+    if not args.no_graph:
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(stream)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            for _ in range(2):
+                vol.insert(imgs, poses, cal)
+                vol.fill_and_clear()
+                vol.project(lo, hi, out=out, count=cnt)
+        torch.cuda.synchronize(dev)
+        for _ in range(2):
+            g.replay()
+        reps = max(1, K // 2)
+        ge0, ge1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        ge0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        ge1.record(stream)
+        torch.cuda.synchronize(dev)
+        graph = {"ms_per_step": ge0.elapsed_time(ge1) / (2 * reps), "steps_per_graph": 2,
+                 "replays": reps}
+        del g
+
     # ---- roofline of the dominant kernel (insertion)
     peak, peak_kind = measured_peaks()
     nvox = nx * ny * nz
@@ -587,7 +617,7 @@ def run_gpu(args):
             "streaming": streaming,
             "variants": variants,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches_per_step * K,
-            "autotune": tune,
+            "autotune": tune, "cuda_graph": graph,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
