@@ -85,3 +85,31 @@ def test_calls_on_null_handle_fail_cleanly(usvol):
     assert L.usv_volume_destroy(None) == usvol.ERR_ARG
     assert usvol.strerror(usvol.ERR_NOMEM).startswith("device storage")
     assert usvol.strerror(12345) == "unknown usvol error"
+
+
+def test_volume_bytes_with_spare_accumulators(usvol):
+    n = 270 * 1840 * 200
+    b = usvol.volume_bytes((270, 1840, 200), usvol.PNN)
+    bs = usvol.volume_bytes((270, 1840, 200), usvol.PNN | usvol.SPARE_ACCUM)
+    assert bs - b == (n * 8 + 255) // 256 * 256
+    bt = usvol.volume_bytes((40, 30, 20), usvol.TRILINEAR | usvol.SPARE_ACCUM)
+    assert bt - usvol.volume_bytes((40, 30, 20), usvol.TRILINEAR) == 40 * 30 * 20 * 8
+    assert usvol.volume_bytes((4, 4, 4), 0x200) == 0
+    assert usvol.volume_bytes((4, 4, 4), usvol.SPARE_ACCUM | 2) == 0
+
+
+def test_new_calls_reject_bad_arguments_on_host(usvol):
+    L = usvol.lib()
+    cfg = usvol.TileConfig(128, 64, 8)
+    assert L.usv_fill_holes_and_clear(None, 1, None) == usvol.ERR_ARG
+    assert L.usv_set_tile_config(None, 4, 4, ctypes.byref(cfg)) == usvol.ERR_ARG
+    assert L.usv_get_tile_config(None, 4, 4, ctypes.byref(cfg)) == usvol.ERR_ARG
+    assert L.usv_tune_insert(None, None, 1, 4, 4, 0, None, None, None, ctypes.c_size_t(0),
+                             None, None, None) == usvol.ERR_ARG
+    # multi-job insertion: the job list is checked before any device work
+    assert L.usv_insert_frames_multi(None, 0, None) == usvol.OK
+    assert L.usv_insert_frames_multi(None, 1, None) == usvol.ERR_ARG
+    assert L.usv_insert_frames_multi(None, -1, None) == usvol.ERR_ARG
+    jobs = (usvol.InsertJob * 33)()
+    assert L.usv_insert_frames_multi(jobs, 33, None) == usvol.ERR_RANGE
+    assert L.usv_insert_frames_multi(jobs, 2, None) == usvol.ERR_ARG   # null volumes
