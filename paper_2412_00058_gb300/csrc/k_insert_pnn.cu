@@ -8,11 +8,11 @@
 // GB300 design:
 //  * one CTA = a tile of TW columns x TH rows of FPC consecutive frames
 //    (default 128 x 64 x 8; TW is 64, 128 or 256, the shape is set per frame
-//    size or chosen by the autotuner); a row segment of TW pixels is TW/8
-//    lanes, each lane eight consecutive pixels read with one coalesced
-//    64-bit load (the next row's load is issued before the current row is
-//    processed).  With the default a half-warp covers one row and the CTA's
-//    16 half-warps take every 16th row.  The near-square tile keeps the box
+//    size or chosen by the autotuner); a row segment of TW pixels is TW/16
+//    lanes, each lane sixteen consecutive pixels read with one coalesced
+//    128-bit load (the next row's load is issued before the current row is
+//    processed).  With the default a quarter-warp covers one row and the
+//    CTA's 32 quarter-warps take every 32nd row.  The near-square tile keeps the box
 //    small: the frames are tilted in plane, and an axis-aligned box around a
 //    tilted 128 x 64 patch holds about 0.09 entries per pixel against 0.13
 //    for a 256 x 32 patch;
@@ -21,9 +21,10 @@
 //    accumulate into a dense shared-memory box and then add each touched
 //    entry to HBM with one packed 64-bit global atomic;
 //  * per pixel: three exact 64-bit coordinate adds, the box index, one
-//    native 32-bit shared atomic.  In one step all 32 lanes handle pixels 8
-//    columns apart, i.e. (nearly always) different voxels, so the atomics
-//    neither diverge nor collide;
+//    native 32-bit shared atomic.  In one step the lanes of a row segment
+//    handle pixels 16 columns apart (different voxels), so the atomics do
+//    not diverge; lanes of the warp's other rows may meet them in a voxel
+//    (a bank conflict, not a divergence);
 //  * box entry layout: if the frames' bound on pixels per voxel (set-up
 //    kernel) keeps every count of the CTA below 1024, one word holds
 //    count (10 bits) | sum (22 bits) -> one atomic per pixel; otherwise
@@ -31,7 +32,7 @@
 //    shared memory (pixels as coarse as voxels, steep poses) every pixel
 //    goes straight to an HBM atomic;
 //  * bounds checks run only in tiles whose box was clipped by the grid, and
-//    there once per 8-pixel group: along a row every voxel index is monotone,
+//    there once per 16-pixel group: along a row every voxel index is monotone,
 //    so a group whose two end pixels are inside the box is inside.
 #include <climits>
 
@@ -43,7 +44,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kPix = 8;              // pixels per lane per row (one 64-bit load)
+constexpr int kPix = 16;             // pixels per lane per row (one 128-bit load)
 constexpr int kSmem = 48 * 1024;     // dynamic shared memory per CTA (the box)
 constexpr int kMaxFpc = 8;           // frames per CTA (warp 0 takes 4 corners x 8 frames)
 
@@ -128,11 +129,12 @@ template <int J, bool CHECK, int MODE>
 __device__ __forceinline__ void put_px(unsigned *box, unsigned cap, unsigned long long *acc,
                                        long long qx, long long qy, long long qz, long long Ax,
                                        long long Ay, long long Az, unsigned ex, unsigned ey,
-                                       unsigned ez, uint2 w, int npx)
+                                       unsigned ez, uint4 w, int npx)
 {
     if constexpr (J < kPix) {
         if (J < npx)
-            put<CHECK, MODE, J & 3>(box, cap, acc, qx, qy, qz, ex, ey, ez, J < 4 ? w.x : w.y);
+            put<CHECK, MODE, J & 3>(box, cap, acc, qx, qy, qz, ex, ey, ez,
+                                    J < 4 ? w.x : J < 8 ? w.y : J < 12 ? w.z : w.w);
         put_px<J + 1, CHECK, MODE>(box, cap, acc, qx + Ax, qy + Ay, qz + Az, Ax, Ay, Az, ex, ey,
                                    ez, w, npx);
     }
@@ -142,7 +144,7 @@ template <bool CHECK, int MODE>
 __device__ __forceinline__ void put_group(unsigned *box, unsigned cap, unsigned long long *acc,
                                           long long qx, long long qy, long long qz, long long Ax,
                                           long long Ay, long long Az, unsigned ex, unsigned ey,
-                                          unsigned ez, uint2 w, int npx)
+                                          unsigned ez, uint4 w, int npx)
 {
     put_px<0, CHECK, MODE>(box, cap, acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w, npx);
 }
@@ -185,25 +187,29 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
         long long qx = qx0, qy = qy0, qz = qz0;
         const uint8_t *src = a.img + ((size_t)f * a.H + v) * a.W + u;
         auto load = [&](const uint8_t *p) {
-            uint2 w;
+            uint4 w;
             if (VEC) {
-                w = __ldcs(reinterpret_cast<const uint2 *>(p));
+                w = __ldcs(reinterpret_cast<const uint4 *>(p));
             } else {
-                w = make_uint2(0u, 0u);
+                w = make_uint4(0u, 0u, 0u, 0u);
                 for (int j = 0; j < npx; ++j) {
-                    const unsigned b = __ldcs(p + j);
+                    const unsigned b = __ldcs(p + j) << (8 * (j & 3));
                     if (j < 4)
-                        w.x |= b << (8 * j);
+                        w.x |= b;
+                    else if (j < 8)
+                        w.y |= b;
+                    else if (j < 12)
+                        w.z |= b;
                     else
-                        w.y |= b << (8 * (j - 4));
+                        w.w |= b;
                 }
             }
             return w;
         };
-        uint2 w = load(src);
+        uint4 w = load(src);
         for (; v < v1; v += kPassRows) {
             const bool more = v + kPassRows < v1;
-            uint2 wn = make_uint2(0u, 0u);
+            uint4 wn = make_uint4(0u, 0u, 0u, 0u);
             if (more)
                 wn = load(src + rstep);
             bool inside = true;
