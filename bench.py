@@ -404,7 +404,7 @@ def run_gpu(args):
         t_t0 = time.perf_counter()
         tile, tile_ms = vol.tune(imgs, poses, cal, stream)
         tune = {"tile": list(tile), "default": [128, 64, 8],
-                "insert_ms_first_1024_frames": tile_ms, "candidates": 18,
+                "insert_ms_first_1024_frames": tile_ms, "candidates": 45,
                 "seconds": time.perf_counter() - t_t0}
     vol.reset(stream)
     for _ in range(max(args.warmup, 3)):

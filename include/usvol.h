@@ -273,7 +273,7 @@ int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *str
  * `stream` (the call waits for the stream), and keeps the fastest shape in
  * the volume for frames of H x W.  The volume's own accumulators are not
  * touched (its per-frame set-up scratch is).  Candidates: USV_PNN tile_w
- * {64, 128, 256} x tile_h {32, 64, 128} x frames_per_cta {4, 8};
+ * {64, 128, 256} x tile_h {32, 48, 64, 96, 128} x frames_per_cta {4, 6, 8};
  * USV_TRILINEAR tile_h {16, 32, 64, 128} x frames_per_cta {2, 4, 8}.
  *   scratch_dev    device, 16-byte aligned, >= 8 * nx * ny * nz bytes
  *   best_out       the chosen shape (may be NULL)

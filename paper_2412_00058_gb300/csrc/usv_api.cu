@@ -605,7 +605,7 @@ int tune_candidates(int mode, TileCfg *out)
     int k = 0;
     if (mode == USV_PNN) {
         out[k++] = kPnnTileDefault;
-        const int tw[3] = {64, 128, 256}, th[3] = {32, 64, 128}, fpc[2] = {4, 8};
+        const int tw[3] = {64, 128, 256}, th[5] = {32, 48, 64, 96, 128}, fpc[3] = {4, 6, 8};
         for (int a : tw)
             for (int b : th)
                 for (int c : fpc) {
@@ -667,7 +667,7 @@ int usv_tune_insert(usv_volume *vol, const void *images_dev, int32_t n, int32_t 
     if (scratch_bytes < acc_bytes)
         return USV_ERR_NOMEM;
     const int nt = n < 1024 ? n : 1024;
-    usv::TileCfg cand[32];
+    usv::TileCfg cand[64];
     const int ncand = usv::tune_candidates(v.mode, cand);
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);

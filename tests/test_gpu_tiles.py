@@ -54,7 +54,8 @@ def run_with_tile(w, cfg, tune=False):
     return res
 
 
-PNN_SHAPES = [(tw, th, f) for tw in (64, 128, 256) for th in (32, 64, 128) for f in (4, 8)]
+PNN_SHAPES = [(tw, th, f) for tw in (64, 128, 256) for th in (32, 48, 64, 96, 128)
+              for f in (4, 6, 8)]
 PNN_SHAPES += [(128, 7, 3), (64, 1, 1), (256, 200, 8), (64, 640, 2)]
 
 
