@@ -557,19 +557,11 @@ cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaS
     const dim3 grid = fill_grid(a, FTX, FTY, 4 * 6, lo, hi, v.num_sms, 16);
     if (grid.x == 0 || grid.y == 0 || grid.z == 0)
         return cudaSuccess;
-    static int attr_device = -1;
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (attr_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(
-            k_fill_pnn<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFillSmemCp);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fill_pnn<true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kFillSmemTma);
-        if (e != cudaSuccess)
-            return e;
-        attr_device = dev;
-    }
+    cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(k_fill_pnn<false>), kFillSmemCp);
+    if (e == cudaSuccess)
+        e = prepare_kernel(reinterpret_cast<const void *>(k_fill_pnn<true>), kFillSmemTma);
+    if (e != cudaSuccess)
+        return e;
     alignas(64) CUtensorMap map, cmap;
     std::memset(&cmap, 0, sizeof(cmap));
     if (acc_tensor_map(v, v.acc, kTmaW, FPY, &map) &&

@@ -416,19 +416,11 @@ template <int TW>
 cudaError_t launch_tw(const PnnArgs &a, dim3 grid, bool vec, cudaStream_t st)
 {
     // the box plus the CTA's static words exceed the 48 KB default
-    static int attr_device = -1;
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (attr_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn<TW, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_insert_pnn<TW, false>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e != cudaSuccess)
-            return e;
-        attr_device = dev;
-    }
+    cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(k_insert_pnn<TW, true>), kSmem);
+    if (e == cudaSuccess)
+        e = prepare_kernel(reinterpret_cast<const void *>(k_insert_pnn<TW, false>), kSmem);
+    if (e != cudaSuccess)
+        return e;
     if (vec)
         k_insert_pnn<TW, true><<<grid, kThreads, kSmem, st>>>(a);
     else
@@ -494,20 +486,11 @@ cudaError_t launch_insert_pnn_multi(const InsertJob *jobs, int njobs, int num_sm
     const long long total = J.begin[njobs];
     if (total == 0)
         return cudaSuccess;
-    static int attr_device = -1, per_sm = 1;
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (attr_device != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_insert_pnn_multi,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_insert_pnn_multi,
-                                                              kThreads, kSmem);
-        if (e != cudaSuccess)
-            return e;
-        per_sm = per_sm < 1 ? 1 : per_sm;
-        attr_device = dev;
-    }
+    int per_sm = 1;
+    const cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(k_insert_pnn_multi), kSmem,
+                                         kThreads, &per_sm);
+    if (e != cudaSuccess)
+        return e;
     const long long resident = (long long)num_sms * per_sm;
     const unsigned grid = (unsigned)(total < resident ? total : resident);
     k_insert_pnn_multi<<<grid, kThreads, kSmem, st>>>(J);

@@ -370,15 +370,11 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
-    static int attr_device = -1;
-    int dev = -1;
-    cudaGetDevice(&dev);
-    if (attr_device != dev) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_insert_trilinear, cudaFuncAttributeMaxDynamicSharedMemorySize, kBoxBytes);
+    if (kUseBox) {
+        const cudaError_t e =
+            prepare_kernel(reinterpret_cast<const void *>(k_insert_trilinear), kBoxBytes);
         if (e != cudaSuccess)
             return e;
-        attr_device = dev;
     }
     dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
     k_insert_trilinear<<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);

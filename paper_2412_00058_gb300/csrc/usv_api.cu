@@ -4,6 +4,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 
@@ -795,4 +797,36 @@ int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *str
     if (e == cudaSuccess)
         e = usv::launch_insert_pnn_multi(ij, m, num_sms, st);
     return usv::cuda_rc(e);
+}
+
+// ---- per-(kernel, device) launch preparation ----
+
+cudaError_t usv::prepare_kernel(const void *func, int dyn_smem, int threads, int *blocks_per_sm)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;  // -> blocks per SM (0: not asked)
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(func, dev);
+    auto it = done.find(key);
+    if (it == done.end()) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem);
+        if (e != cudaSuccess)
+            return e;
+        it = done.emplace(key, 0).first;
+    }
+    if (blocks_per_sm) {
+        if (it->second == 0) {
+            int b = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, func, threads, dyn_smem);
+            if (e != cudaSuccess)
+                return e;
+            it->second = b < 1 ? 1 : b;
+        }
+        *blocks_per_sm = it->second;
+    }
+    return cudaSuccess;
 }

@@ -100,6 +100,13 @@ struct InsertJob {
     TileCfg cfg;  // tile_w must be 128
 };
 
+// Raises `func`'s dynamic shared-memory limit to dyn_smem on the current
+// device, once per (kernel, device) and safely from several host threads;
+// with blocks_per_sm, also returns how many blocks of `threads` threads fit
+// on one SM at that size.
+cudaError_t prepare_kernel(const void *func, int dyn_smem, int threads = 0,
+                           int *blocks_per_sm = nullptr);
+
 // ---- launchers (each in its own translation unit) ----
 cudaError_t launch_frame_setup(const double *poses, int n, const SetupParams &sp, FrameRec *rec,
                                uint32_t *status, cudaStream_t st);

@@ -109,3 +109,46 @@ def test_multi_insert_errors():
     vols = [usvol.Volume(w.grid, w.spacing, w.origin, "pnn") for _ in range(33)]
     assert code([(v, i, p, c) for v in vols]) == usvol.ERR_RANGE
     usvol.insert_frames_multi([])  # nothing to do
+
+
+def test_volumes_driven_from_several_host_threads():
+    """Four host threads, each with its own volume and stream (insert, fill
+    with clearing, projection): each equals the same work done alone."""
+    import threading
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    ws = [synth.tiny_pnn(seed=40 + k, n=20, H=64, W=64, grid=(64, 64, 64), sweep_mm=5.0,
+                         band=(20, 40))
+          for k in range(4)]
+    dev = [_on_device(w) for w in ws]
+    vols = [usvol.Volume(w.grid, w.spacing, w.origin, "pnn", spare=True) for w in ws]
+    outs = [None] * 4
+    errors = []
+
+    def work(k):
+        try:
+            st = torch.cuda.Stream()
+            with torch.cuda.stream(st):
+                v = vols[k]
+                v.reset(st)
+                for _ in range(3):
+                    v.insert(*dev[k], stream=st)
+                    v.fill_and_clear(st)
+                outs[k] = v.project(*ws[k].band, stream=st)
+            st.synchronize()
+        except Exception as e:  # reported in the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=work, args=(k,)) for k in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors
+    for k, w in enumerate(ws):
+        ref = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+        ref.reset()
+        ref.insert(*dev[k])
+        ref.fill()
+        out, cnt = ref.project(*w.band)
+        assert torch.equal(outs[k][0], out) and torch.equal(outs[k][1], cnt)
