@@ -184,10 +184,10 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel_file: str = "paper_2412_00058_gb300/csrc/k_insert_pnn.cu",
-                     record: str = "profiles/insert_pnn_whole_spine_traffic.txt"):
-    """DRAM bytes per launch of the insertion kernel from the committed ncu
-    record, or None if the kernel source changed since it was taken."""
+def insert_record(kernel_file: str = "paper_2412_00058_gb300/csrc/k_insert_pnn.cu",
+                  record: str = "profiles/insert_pnn_whole_spine_traffic.txt") -> dict:
+    """The committed ncu record of the insertion kernel, or {} if the kernel
+    source changed since it was taken."""
     import hashlib
     try:
         with open(os.path.join(ROOT, kernel_file), "rb") as f:
@@ -198,10 +198,17 @@ def recorded_traffic(kernel_file: str = "paper_2412_00058_gb300/csrc/k_insert_pn
                 if "=" in line and not line.lstrip().startswith("#"):
                     k, v = line.split("=", 1)
                     kv[k.strip()] = v.strip()
-        if kv.get("source_sha256") != sha:
-            return None
+        return kv if kv.get("source_sha256") == sha else {}
+    except OSError:
+        return {}
+
+
+def recorded_traffic() -> float | None:
+    """DRAM bytes per launch of the insertion kernel (committed ncu record)."""
+    kv = insert_record()
+    try:
         return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
-    except (OSError, KeyError, ValueError):
+    except (KeyError, ValueError):
         return None
 
 
@@ -592,6 +599,22 @@ def run_gpu(args):
                "sample": f"{desc}; {cpu_work:.1f} s of CPU work"}
 
     clocks = sampler.summary(t0, t1) if sampler else None
+    # the insertion kernel against the instruction-issue roofline: 4 warp
+    # schedulers per SM, one warp instruction each per clock, at the SM clock
+    # sampled while timing (the maximum clock if there was no sample)
+    issue = None
+    kv = insert_record()
+    if "warp_inst_per_pixel" in kv:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+        if mhz:
+            ipp = float(kv["warp_inst_per_pixel"])
+            got = ipp * w.n * w.H * w.W / (ins_ms / 1e3)
+            top = sms * 4 * mhz * 1e6
+            issue = {"bound": "issue", "achieved": got, "peak": top, "unit": "warp-instr/s",
+                     "frac": got / top, "warp_inst_per_pixel": ipp,
+                     "source": "warp instructions per pixel from the committed ncu record of "
+                               "the same kernel source; peak = SMs x 4 schedulers x SM clock"}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
@@ -608,6 +631,7 @@ def run_gpu(args):
                          "traffic": recorded_traffic() if args.frames >= 3600 else None,
                          "kernel": "insert (PNN)",
                          "algorithmic_bytes": ins_bytes, "peak_kind": peak_kind},
+            "issue_roofline": issue,
             "pipeline_roofline": {"algorithmic_bytes_per_step": step_bytes,
                                   "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
                                   "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak},
