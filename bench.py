@@ -55,6 +55,11 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="usvol", choices=["usvol", "reference"])
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--variants-only", action="store_true",
+                   help="run only the variant rows (for profiling them)")
+    p.add_argument("--variant-frames", type=int, default=0,
+                   help="convex sweep variant: only this many frames, into the y-slab they "
+                        "cover (a small case for profiling)")
     p.add_argument("--no-graph", action="store_true",
                    help="skip the CUDA-graph replay of the step")
     p.add_argument("--no-tune", action="store_true",
@@ -259,7 +264,7 @@ def oracle_sweep_seconds(w, frac: float, rng_offset: int = 0, acc=None):
     return sweep, desc, t_ins + t_fp
 
 
-def measure_variants(dev, reps: int = 5):
+def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
     """Event-timed variant rows: the full convex-fan sweep with trilinear
     splatting (3000 frames 512x512 -> 400x1700x400), and one evaluation of
     the pose-refinement loss + gradient (512 FP32 frames 256x256 ->
@@ -269,12 +274,16 @@ def measure_variants(dev, reps: int = 5):
     from paper_2412_00058_gb300 import posegrad, synth, usvol
     out = {}
     stream = torch.cuda.current_stream(dev)
-    w = synth.convex_fan()
+    if frames:  # the first `frames` frames of the sweep, into the y-slab they cover
+        ny = int(660.0 * frames / 2999.0 / 0.4) + 60
+        w = synth.convex_fan(n=frames, grid=(400, ny, 400), sweep_mm=660.0 * frames / 2999.0)
+    else:
+        w = synth.convex_fan()
     vol = usvol.Volume(w.grid, w.spacing, w.origin, "trilinear", device=dev)
     imgs = torch.from_numpy(w.images).to(dev)
     poses = torch.from_numpy(w.poses).to(dev)
     cal = usvol.calibration_of(w)
-    tri_tile, _ = vol.tune(imgs, poses, cal, stream)
+    tri_tile = vol.tune(imgs, poses, cal, stream)[0] if tune else vol.get_tile(w.H, w.W)
     nx, ny, nz = w.grid
     img_out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     cnt = torch.empty((ny, nx), dtype=torch.int16, device=dev)
@@ -296,7 +305,8 @@ def measure_variants(dev, reps: int = 5):
     ins = float(np.median([t[1] for t in ts]))
     samples = w.n * w.H * w.W
     out["trilinear_convex_sweep"] = {
-        "workload": "3000 convex frames 512x512 uint8 (60 deg, 120 mm) -> 400x1700x400 @ 0.4 mm",
+        "workload": f"{w.n} convex frames 512x512 uint8 (60 deg, 120 mm) -> "
+                    f"{w.grid[0]}x{w.grid[1]}x{w.grid[2]} @ 0.4 mm",
         "ms_per_sweep": step, "frames_per_s": w.n / step * 1e3,
         "insert_ms": ins, "samples_per_s": samples / ins * 1e3, "tile": list(tri_tile)}
     del vol, imgs, poses
@@ -376,6 +386,11 @@ def run_gpu(args):
         build.build()
     barrier(dev)
     usvol.lib()
+    if args.variants_only:
+        if rank == 0:
+            print(json.dumps({"variants": measure_variants(dev, frames=args.variant_frames,
+                                                           tune=not args.no_tune)}), flush=True)
+        return 0
 
     w = sweep_workload(args.frames)
     nx, ny, nz = w.grid
@@ -586,7 +601,7 @@ def run_gpu(args):
     # ---- variant rows: trilinear convex sweep, pose gradient (one GPU)
     variants = None
     if not args.no_variants and world == 1:
-        variants = measure_variants(dev)
+        variants = measure_variants(dev, frames=args.variant_frames, tune=not args.no_tune)
 
     # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
