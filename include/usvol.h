@@ -261,6 +261,8 @@ typedef struct {
     int32_t dtype;           /* USV_U8 */
     const double *poses_dev; /* [n][16] row-major probe->world, mm */
     const usv_calibration *cal;
+    const int32_t *first_rows_dev; /* [n] first inserted row per frame, as for
+                                      usv_insert_frames_cut(); NULL: all rows */
 } usv_insert_job;
 
 int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *stream);

@@ -778,7 +778,7 @@ int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *str
         s.sp.sx = b.cal->sx_mm;
         s.sp.sy = b.cal->sy_mm;
         s.sp.convex = 0;
-        s.sp.first_rows = nullptr;
+        s.sp.first_rows = b.first_rows_dev;
         s.rec = v.rec;
         s.status = v.status;
         sj.begin[m + 1] = sj.begin[m] + b.n;

@@ -68,7 +68,7 @@ class InsertJob(ctypes.Structure):
     _fields_ = [("vol", ctypes.c_void_p), ("images_dev", ctypes.c_void_p),
                 ("n", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
                 ("dtype", ctypes.c_int32), ("poses_dev", ctypes.c_void_p),
-                ("cal", ctypes.c_void_p)]
+                ("cal", ctypes.c_void_p), ("first_rows_dev", ctypes.c_void_p)]
 
 
 class Calibration(ctypes.Structure):
@@ -264,15 +264,21 @@ def fill_holes(handle: int, radius: int = 1, stream=None) -> None:
 
 
 def insert_frames_multi(jobs, stream=None) -> None:
-    """jobs: sequence of (Volume, images [n,H,W] u8, poses [n,4,4] f64, Calibration)."""
+    """jobs: sequence of (Volume, images [n,H,W] u8, poses [n,4,4] f64, Calibration)
+    or (..., first_rows [n] int32 on the device) for tissue-segmented frames."""
     arr = (InsertJob * max(len(jobs), 1))()
     keep = []
-    for k, (vol, images, poses, cal) in enumerate(jobs):
+    for k, job in enumerate(jobs):
+        vol, images, poses, cal = job[:4]
+        rows = job[4] if len(job) > 4 else None
         assert images.is_cuda and poses.is_cuda and images.is_contiguous() and poses.is_contiguous()
+        if rows is not None:
+            assert rows.is_cuda and rows.dtype == torch.int32 and rows.is_contiguous()
         n, H, W = images.shape
         keep.append(cal)
         arr[k] = InsertJob(vol.handle, images.data_ptr(), n, H, W, U8, poses.data_ptr(),
-                           ctypes.cast(ctypes.pointer(cal), ctypes.c_void_p))
+                           ctypes.cast(ctypes.pointer(cal), ctypes.c_void_p),
+                           rows.data_ptr() if rows is not None else None)
     _check(lib().usv_insert_frames_multi(arr, len(jobs), ctypes.c_void_p(_stream_ptr(stream))),
            "usv_insert_frames_multi")
 

@@ -152,3 +152,29 @@ def test_volumes_driven_from_several_host_threads():
         ref.fill()
         out, cnt = ref.project(*w.band)
         assert torch.equal(outs[k][0], out) and torch.equal(outs[k][1], cnt)
+
+
+def test_multi_insert_with_tissue_cut_rows():
+    """Per-frame first rows (tissue segmentation) in a multi-job insertion
+    equal usv_insert_frames_cut of each job."""
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    ws = [synth.whole_spine(n=30, grid=(270, 80, 200), y_start_mm=3.0, y_span_mm=10.0),
+          synth.tiny_pnn(n=20)]
+    rng = np.random.default_rng(9)
+    jobs, alone = [], []
+    for w in ws:
+        i, p, c = _on_device(w)
+        rows = torch.from_numpy(rng.integers(-5, w.H + 5, w.n).astype(np.int32)).cuda()
+        vm = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+        va = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+        vm.reset()
+        va.reset()
+        usvol.insert_frames_cut(va.handle, i.data_ptr(), w.n, w.H, w.W, usvol.U8, p.data_ptr(),
+                                c, rows.data_ptr())
+        jobs.append((vm, i, p, c, rows))
+        alone.append(va)
+    usvol.insert_frames_multi(jobs)
+    for (vm, *_), va in zip(jobs, alone):
+        assert np.array_equal(_accum(vm), _accum(va))
+        assert _accum(vm).any()
