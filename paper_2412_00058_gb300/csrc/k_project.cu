@@ -5,14 +5,18 @@
 //
 // GB300 design: one thread per (x, y) column marching down the band; a warp
 // reads 32 consecutive bytes of a row per plane and shares one mask word.
-// The band is a few MB, so this kernel is launch/latency-bound rather than
-// HBM-bound; it is kept separate so several bands can be projected from one
-// filled volume.
+// The band is a few MB, so this kernel is latency-bound rather than
+// HBM-bound: each thread issues the loads of 8 planes before it uses any of
+// them (the sums still run in ascending z), so their latencies overlap.  It
+// is kept separate so several bands can be projected from one filled
+// volume.
 #include "usv_internal.cuh"
 
 namespace usv {
 
 namespace {
+
+constexpr int kUnroll = 8;  // planes whose loads are in flight together
 
 struct ProjArgs {
     const void *val;
@@ -32,9 +36,24 @@ __global__ void __launch_bounds__(256) k_project_u8(ProjArgs a)
     const size_t plane = (size_t)a.ny * a.nx, mplane = (size_t)a.ny * a.nxw;
     const size_t i0 = (size_t)y * a.nx + x, m0 = (size_t)y * a.nxw + (x >> 5);
     unsigned s = 0, c = 0;
-    for (int z = a.lo; z < a.hi; ++z) {
-        const unsigned bit = (__ldg(a.mask + m0 + z * mplane) >> (x & 31)) & 1u;
-        const unsigned v = __ldg(val + i0 + z * plane);
+    int z = a.lo;
+    for (; z + kUnroll <= a.hi; z += kUnroll) {
+        unsigned m[kUnroll], v[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            m[k] = __ldg(a.mask + m0 + (size_t)(z + k) * mplane);
+            v[k] = __ldg(val + i0 + (size_t)(z + k) * plane);
+        }
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            const unsigned bit = (m[k] >> (x & 31)) & 1u;
+            s += bit ? v[k] : 0u;
+            c += bit;
+        }
+    }
+    for (; z < a.hi; ++z) {
+        const unsigned bit = (__ldg(a.mask + m0 + (size_t)z * mplane) >> (x & 31)) & 1u;
+        const unsigned v = __ldg(val + i0 + (size_t)z * plane);
         s += bit ? v : 0u;
         c += bit;
     }
@@ -53,10 +72,26 @@ __global__ void __launch_bounds__(256) k_project_f32(ProjArgs a)
     const size_t i0 = (size_t)y * a.nx + x, m0 = (size_t)y * a.nxw + (x >> 5);
     float s = 0.0f;
     unsigned c = 0;
-    for (int z = a.lo; z < a.hi; ++z) {
-        const unsigned bit = (__ldg(a.mask + m0 + z * mplane) >> (x & 31)) & 1u;
+    int z = a.lo;
+    for (; z + kUnroll <= a.hi; z += kUnroll) {
+        unsigned m[kUnroll];
+        float v[kUnroll];
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k) {
+            m[k] = __ldg(a.mask + m0 + (size_t)(z + k) * mplane);
+            v[k] = __ldg(val + i0 + (size_t)(z + k) * plane);
+        }
+#pragma unroll
+        for (int k = 0; k < kUnroll; ++k)
+            if ((m[k] >> (x & 31)) & 1u) {  // ascending z, as one plane at a time
+                s += v[k];
+                c += 1;
+            }
+    }
+    for (; z < a.hi; ++z) {
+        const unsigned bit = (__ldg(a.mask + m0 + (size_t)z * mplane) >> (x & 31)) & 1u;
         if (bit) {
-            s += __ldg(val + i0 + z * plane);
+            s += __ldg(val + i0 + (size_t)z * plane);
             c += 1;
         }
     }

@@ -144,7 +144,9 @@ cudaError_t launch_frame_setup(const double *poses, int n, const SetupParams &sp
 {
     if (n <= 0)
         return cudaSuccess;
-    k_frame_setup<<<(n + 127) / 128, 128, 0, st>>>(poses, n, sp, rec, status);
+    // one warp per block: the FP64 work per frame is long, so spread the
+    // frames over as many SMs as possible
+    k_frame_setup<<<(n + 31) / 32, 32, 0, st>>>(poses, n, sp, rec, status);
     return cudaGetLastError();
 }
 
@@ -153,7 +155,7 @@ cudaError_t launch_frame_setup_multi(const SetupJobs &jobs, cudaStream_t st)
     const int total = jobs.begin[jobs.njobs];
     if (total <= 0)
         return cudaSuccess;
-    k_frame_setup_multi<<<(total + 127) / 128, 128, 0, st>>>(jobs);
+    k_frame_setup_multi<<<(total + 31) / 32, 32, 0, st>>>(jobs);
     return cudaGetLastError();
 }
 
