@@ -663,6 +663,13 @@ def run_gpu(args):
                          "kernel": "insert (PNN)",
                          "algorithmic_bytes": ins_bytes, "peak_kind": peak_kind},
             "issue_roofline": issue,
+            "stage_rooflines": {
+                "fill_and_clear": {"algorithmic_bytes": fill_bytes + clear_bytes,
+                                   "achieved_gbs": (fill_bytes + clear_bytes) / (fill_ms / 1e3) / 1e9,
+                                   "frac": (fill_bytes + clear_bytes) / (fill_ms / 1e3) / 1e9 / peak},
+                "project": {"algorithmic_bytes": proj_bytes,
+                            "achieved_gbs": proj_bytes / (proj_ms / 1e3) / 1e9,
+                            "frac": proj_bytes / (proj_ms / 1e3) / 1e9 / peak}},
             "pipeline_roofline": {"algorithmic_bytes_per_step": step_bytes,
                                   "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
                                   "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak},
