@@ -396,6 +396,19 @@ int usv_insert_pnn_noalloc(uint64_t *accum_dev, usv_grid grid, const double spac
                            int32_t H, int32_t W, const double *poses_dev,
                            const usv_calibration *cal, uint32_t *status_dev, void *stream);
 
+/* ------------------------------------------------------------------------
+ * usv_test_fill_wait_timeout -- for testing the device-side failure path
+ * only (no counterpart in the paper).  Runs usv_fill_holes() with the copy
+ * of plane `plane` (0 <= plane < nz) never issued, so the fill kernel's
+ * bounded wait for it runs out after about one second: the kernel sets
+ * USV_STATUS_TIMEOUT, waits (bounded) for its copies still in flight and
+ * returns.  The values and mask written by this call are undefined; the
+ * accumulators are untouched and the volume stays usable.
+ * USV_ERR_UNSUPPORTED unless the fill takes its tensor-copy path (USV_PNN,
+ * even nx), the only one that waits on the device.
+ * ---------------------------------------------------------------------- */
+int usv_test_fill_wait_timeout(usv_volume *vol, int32_t plane, void *stream);
+
 /* Synchronise `stream`, then return the device status bits (>= 0) and clear
  * them, or a negative USV_ERR_* code. */
 int usv_status(usv_volume *vol, void *stream);

@@ -51,6 +51,7 @@ struct FillArgs {
     int nx, ny, nz, nxw, zchunk;
     int rx0, ry0, rz0, rz1;  // refreshed region: x from rx0 (a multiple of 32), y from ry0, z in [rz0, rz1)
     unsigned long long *clear;  // PNN, whole grid: accumulators to zero in the same pass, or null
+    int withhold = -1;          // test hook: plane (>= 0) whose copy is never issued; -1: none
 };
 
 template <typename T>
@@ -98,7 +99,10 @@ constexpr int kZeroRows = 16;
 constexpr int kZeroBytes = FTX * kZeroRows * 8;
 constexpr int kFillSmemCp = FSLOTS * FPLANE * 8;
 constexpr int kFillSmemTma = FSLOTS * kTmaSlot * 8 + kZeroBytes;
-constexpr unsigned kSpinLimit = 1u << 22;  // bounded mbarrier waits (well over a second)
+// Bounded mbarrier waits: about one second by the global nanosecond timer,
+// and never more than kSpinCap polls.
+constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr unsigned kSpinCap = 1u << 26;
 
 __device__ __forceinline__ void cp_async8(unsigned saddr, const void *gmem, bool valid)
 {
@@ -131,11 +135,24 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
     return done != 0u;
 }
 // true once the phase with this parity has completed; false after the limit
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// true once the phase with this parity has completed; false after the limit
 __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity)
 {
-    for (unsigned i = 0; i < kSpinLimit; ++i)
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned i = 0; i < kSpinCap; ++i) {
         if (mbar_try_wait(bar, parity))
             return true;
+        if ((i & 63u) == 63u && global_ns() - t0 > kWaitNs)
+            return false;
+    }
     return false;
 }
 __device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int x, int y,
@@ -214,7 +231,8 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
     }
     auto issue = [&](int pl) {
         if (TMA) {
-            if (tid == 0 && pl <= z1) {
+            // (plane -1 is a real ring entry: the zero plane below the grid)
+            if (tid == 0 && pl <= z1 && (a.withhold < 0 || pl != a.withhold)) {
                 const int s = (pl + FSLOTS) % FSLOTS;
                 mbar_expect_tx(bbase + 8u * s, kTmaBytes);
                 // outside the grid (x < 0, y < 0, z < 0, beyond the far
@@ -546,10 +564,10 @@ bool acc_tensor_map(const Volume &v, const void *acc, int box_x, int box_y, CUte
 }  // namespace
 
 cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st,
-                            void *clear)
+                            void *clear, int withhold)
 {
     FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0,
-               static_cast<unsigned long long *>(clear)};
+               static_cast<unsigned long long *>(clear), withhold};
     if (clear && (lo[0] != 0 || lo[1] != 0 || lo[2] != 0 || hi[0] != v.g.nx ||
                   hi[1] != v.g.ny || hi[2] != v.g.nz))
         return cudaErrorInvalidValue;  // clearing covers the whole grid only
@@ -567,6 +585,8 @@ cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaS
     if (acc_tensor_map(v, v.acc, kTmaW, FPY, &map) &&
         (!clear || acc_tensor_map(v, clear, FTX, kZeroRows, &cmap))) {
         k_fill_pnn<true><<<grid, dim3(FTX, FBY), kFillSmemTma, st>>>(a, map, cmap);
+    } else if (withhold >= 0) {
+        return cudaErrorNotSupported;  // only the tensor-copy path waits on the device
     } else {
         std::memset(&map, 0, sizeof(map));
         k_fill_pnn<false><<<grid, dim3(FTX, FBY), kFillSmemCp, st>>>(a, map, cmap);

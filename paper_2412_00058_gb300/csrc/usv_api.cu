@@ -830,3 +830,21 @@ cudaError_t usv::prepare_kernel(const void *func, int dyn_smem, int threads, int
     }
     return cudaSuccess;
 }
+
+// ---- test hook for the device-side failure path ----
+
+int usv_test_fill_wait_timeout(usv_volume *vol, int32_t plane, void *stream)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    Volume &v = *reinterpret_cast<Volume *>(vol);
+    if (plane < 0 || plane >= v.g.nz)
+        return USV_ERR_ARG;
+    if (v.mode != USV_PNN || v.g.nx % 2 != 0)
+        return USV_ERR_UNSUPPORTED;
+    const int lo[3] = {0, 0, 0}, hi[3] = {v.g.nx, v.g.ny, v.g.nz};
+    usv::DeviceGuard g(v.device);
+    const cudaError_t e =
+        usv::launch_fill_pnn(v, lo, hi, static_cast<cudaStream_t>(stream), nullptr, plane);
+    return e == cudaErrorNotSupported ? USV_ERR_UNSUPPORTED : usv::cuda_rc(e);
+}

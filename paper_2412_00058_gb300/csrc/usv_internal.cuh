@@ -130,8 +130,10 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
                                     const TileCfg &cfg = kTriTileDefault);
 // fill / project a region: voxels [lo, hi) (clipped to the grid; the fill
 // needs lo[0] a multiple of 32), columns [rlo, rhi)
+// clear: accumulators to zero in the pass; withhold: test hook (a plane whose
+// copy is never issued, so the kernel's bounded wait for it runs out)
 cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaStream_t st,
-                            void *clear = nullptr);  // clear: accumulators to zero in the pass
+                            void *clear = nullptr, int withhold = -1);
 cudaError_t launch_fill_trilinear(const Volume &v, const int *lo, const int *hi, cudaStream_t st);
 cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
                               float *out, uint16_t *cnt, cudaStream_t st);

@@ -38,7 +38,7 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
            "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta",
            "usv_fill_holes_and_clear", "usv_tune_insert", "usv_set_tile_config",
-           "usv_get_tile_config", "usv_insert_frames_multi")
+           "usv_get_tile_config", "usv_insert_frames_multi", "usv_test_fill_wait_timeout")
 
 
 class UsvError(RuntimeError):
@@ -309,6 +309,13 @@ def get_tile_config(handle: int, H: int, W: int) -> tuple:
     _check(lib().usv_get_tile_config(ctypes.c_void_p(handle), H, W, ctypes.byref(out)),
            "usv_get_tile_config")
     return out.as_tuple()
+
+
+def fill_with_withheld_copy(handle: int, plane: int, stream=None) -> None:
+    """Test hook: the fill with one plane copy withheld (its wait runs out)."""
+    _check(lib().usv_test_fill_wait_timeout(ctypes.c_void_p(handle), plane,
+                                            ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_test_fill_wait_timeout")
 
 
 def fill_holes_and_clear(handle: int, radius: int = 1, stream=None) -> None:
