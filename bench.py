@@ -502,6 +502,25 @@ def run_gpu(args):
                  "replays": reps}
         del g
 
+    # ---- the same sweep inserted as it is acquired: 120 calls of 30 frames
+    # (one second at 30 fps each), then fill and projection
+    b30 = None
+    if not args.no_graph:
+        reps30 = 20
+        torch.cuda.synchronize(dev)
+        be0, be1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        be0.record(stream)
+        for _ in range(reps30):
+            for b0 in range(0, w.n, 30):
+                vol.insert(imgs[b0:b0 + 30], poses[b0:b0 + 30], cal, stream)
+            vol.fill_and_clear(stream)
+            vol.project(lo, hi, out=out, count=cnt, stream=stream)
+        be1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms30 = be0.elapsed_time(be1) / reps30
+        b30 = {"ms_per_sweep": ms30, "frames_per_s": w.n / ms30 * 1e3,
+               "inserts_per_sweep": (w.n + 29) // 30}
+
     # ---- roofline of the dominant kernel (insertion)
     peak, peak_kind = measured_peaks()
     nvox = nx * ny * nz
@@ -679,7 +698,7 @@ def run_gpu(args):
             "streaming": streaming,
             "variants": variants,
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": launches_per_step * K,
-            "autotune": tune, "cuda_graph": graph,
+            "autotune": tune, "cuda_graph": graph, "batches_of_30": b30,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -265,6 +265,33 @@ def test_projection_constant_slice_and_literal():
     assert out[0, 0] == np.float32(61.0 / 3.0) and cnt[0, 0] == 3
 
 
+def test_projection_is_linear_in_the_values_for_a_fixed_mask():
+    """With the same has-data mask, the projection of V1 + V2 is the
+    projection of V1 plus that of V2 (exactly, for values whose column sums
+    divide evenly) and scaling V scales the projection."""
+    rng = np.random.default_rng(23)
+    has = (rng.random((12, 6, 7)) < 0.5).astype(np.uint8)
+    _, cnt = oracle.project_u8(np.zeros_like(has), has, 2, 11)
+    k = np.maximum(cnt.astype(np.int64), 1)
+    # per column, values that are a multiple of the band count there: every
+    # mean is an integer and exact in FP32
+    base1 = rng.integers(0, 5, size=(12, 6, 7)) * k[None]
+    base2 = rng.integers(0, 5, size=(12, 6, 7)) * k[None]
+    v1 = np.minimum(base1, 120).astype(np.uint8)
+    v2 = np.minimum(base2, 120).astype(np.uint8)
+    p1, c1 = oracle.project_u8(v1, has, 2, 11)
+    p2, c2 = oracle.project_u8(v2, has, 2, 11)
+    p12, c12 = oracle.project_u8((v1 + v2).astype(np.uint8), has, 2, 11)
+    assert np.array_equal(c1, c2) and np.array_equal(c1, c12)
+    sums1 = (np.where(has[2:11], v1[2:11], 0).astype(np.int64)).sum(axis=0)
+    sums2 = (np.where(has[2:11], v2[2:11], 0).astype(np.int64)).sum(axis=0)
+    ok = (sums1 % k == 0) & (sums2 % k == 0)   # exact means on both sides
+    assert ok.mean() > 0.5
+    assert np.array_equal(p12[ok], (p1 + p2)[ok])
+    p3, _ = oracle.project_u8((2 * v1).astype(np.uint8), has, 2, 11)
+    assert np.array_equal(p3[ok], (2 * p1)[ok])
+
+
 # ---------------------------------------------------------------- trilinear variant
 
 def _single_frame(H, W, I, pose):
