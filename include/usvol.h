@@ -84,7 +84,9 @@ typedef struct {
  * results do not depend on it, except for the FP32 summation order of the
  * trilinear mode).  USV_PNN: tile_w 64, 128 or 256, tile_h 1..1024,
  * frames_per_cta 1..8; default 128 x 64 x 8.  USV_TRILINEAR: tile_w 256,
- * tile_h 1..128, frames_per_cta 1..8; default 256 x 64 x 4. */
+ * tile_h 1..128, frames_per_cta 1..8; default 256 x 64 x 4.  In USV_PNN,
+ * frames_per_cta is an upper bound: a batch of frames too small to fill
+ * the GPU is spread over more thread blocks with fewer frames each. */
 typedef struct {
     int32_t tile_w, tile_h, frames_per_cta;
 } usv_tile_config;

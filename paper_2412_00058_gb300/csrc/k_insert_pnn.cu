@@ -468,6 +468,12 @@ cudaError_t launch_insert_pnn_multi(const InsertJob *jobs, int njobs, int num_sm
 {
     if (njobs < 0 || njobs > kMaxJobs)
         return cudaErrorInvalidValue;
+    int per_sm = 1;
+    const cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(k_insert_pnn_multi), kSmem,
+                                         kThreads, &per_sm);
+    if (e != cudaSuccess)
+        return e;
+    const long long resident = (long long)num_sms * per_sm;
     PnnJobs J;
     J.njobs = njobs;
     J.begin[0] = 0;
@@ -479,19 +485,26 @@ cudaError_t launch_insert_pnn_multi(const InsertJob *jobs, int njobs, int num_sm
         const int tiles_y = (b.H + J.args[j].th - 1) / J.args[j].th;
         J.tiles[j] = J.args[j].tiles_x * tiles_y;
         J.vec[j] = vec_ok(b.img, b.W) ? 1 : 0;
-        const long long groups = b.n > 0 ? (b.n + b.cfg.frames_per_cta - 1) / b.cfg.frames_per_cta
-                                         : 0;
-        J.begin[j + 1] = J.begin[j] + groups * J.tiles[j];
     }
-    const long long total = J.begin[njobs];
+    // frames per block are upper bounds: while all jobs' work items cannot
+    // fill the resident blocks, every job takes fewer frames per block
+    long long total = 0;
+    for (bool shrink = true; shrink;) {
+        total = 0;
+        bool can = false;
+        for (int j = 0; j < njobs; ++j) {
+            const int n = J.args[j].n, f = J.args[j].fpc;
+            J.begin[j + 1] = J.begin[j] + (long long)(n > 0 ? (n + f - 1) / f : 0) * J.tiles[j];
+            can |= f > 1;
+        }
+        total = J.begin[njobs];
+        shrink = can && total < resident;
+        if (shrink)
+            for (int j = 0; j < njobs; ++j)
+                J.args[j].fpc = (J.args[j].fpc + 1) / 2;
+    }
     if (total == 0)
         return cudaSuccess;
-    int per_sm = 1;
-    const cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(k_insert_pnn_multi), kSmem,
-                                         kThreads, &per_sm);
-    if (e != cudaSuccess)
-        return e;
-    const long long resident = (long long)num_sms * per_sm;
     const unsigned grid = (unsigned)(total < resident ? total : resident);
     k_insert_pnn_multi<<<grid, kThreads, kSmem, st>>>(J);
     return cudaGetLastError();
@@ -517,7 +530,13 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
     a.th = min(cfg.tile_h, H);
     a.tiles_x = (W + cfg.tile_w - 1) / cfg.tile_w;
     const int tiles_y = (H + a.th - 1) / a.th;
+    // frames_per_cta is an upper bound: a batch too small to fill the GPU's
+    // resident blocks (4 per SM at the 48 KB box) takes fewer frames per
+    // block, down to one, so that more blocks share it
     a.fpc = cfg.frames_per_cta;
+    const long long resident = (long long)v.num_sms * 4;
+    while (a.fpc > 1 && (long long)((n + a.fpc - 1) / a.fpc) * a.tiles_x * tiles_y < resident)
+        a.fpc = (a.fpc + 1) / 2;
     const bool vec = (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535 || (long long)a.tiles_x * tiles_y > 0x7FFFFFFFLL)
