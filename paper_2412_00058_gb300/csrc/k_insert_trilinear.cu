@@ -342,7 +342,7 @@ bool tri_tile_ok(const TileCfg &c)
 
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
                                     int W, int convex, double r0, double dr, cudaStream_t st,
-                                    const TileCfg &cfg)
+                                    const TileCfg &cfg, int min_rows)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -366,6 +366,22 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     a.tiles_x = (W + kCols - 1) / kCols;
     a.rows = cfg.tile_h;
     a.fpc = cfg.frames_per_cta;
+    // a batch too small to fill the GPU's resident blocks (3 per SM at this
+    // kernel's registers) takes fewer frames per block, then fewer rows per
+    // tile (down to max(8, min_rows)), so that more blocks share it.  The
+    // tile rows fix where each column's walk is anchored, so callers that
+    // must reproduce the positions (the pose gradient) keep them.
+    const int floor_rows = min_rows > 8 ? min_rows : 8;
+    const long long resident = (long long)v.num_sms * 3;
+    auto blocks = [&] {
+        return (long long)a.tiles_x * ((H + a.rows - 1) / a.rows) * ((n + a.fpc - 1) / a.fpc);
+    };
+    while (blocks() < resident && (a.fpc > 1 || a.rows > floor_rows)) {
+        if (a.fpc > 1)
+            a.fpc = (a.fpc + 1) / 2;
+        else
+            a.rows = (a.rows + 1) / 2 < floor_rows ? floor_rows : (a.rows + 1) / 2;
+    }
     const int tiles_y = (H + a.rows - 1) / a.rows;
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)

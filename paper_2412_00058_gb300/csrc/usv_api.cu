@@ -209,7 +209,7 @@ namespace usv {
 int insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                 int32_t dtype, const double *poses_dev, const usv_calibration *cal,
                 const int32_t *first_rows_dev, void *stream, void *acc_override = nullptr,
-                const TileCfg *cfg_override = nullptr);
+                const TileCfg *cfg_override = nullptr, int tri_min_rows = 8);
 }
 
 int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
@@ -304,9 +304,12 @@ int usv_pose_loss_grad(usv_volume *vol, const void *images_dev, int32_t n, int32
         return USV_ERR_ARG;
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the gradient kernel recomputes every sample on 64-row tiles, so the
+    // forward splat keeps 64-row tiles (same column anchors, same cells)
     int rc = usv_volume_reset(vol, stream);
     if (rc == USV_OK)
-        rc = usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream);
+        rc = usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream,
+                              nullptr, &usv::kTriTileDefault, usv::kTriTileDefault.tile_h);
     if (rc != USV_OK)
         return rc;
     cudaError_t e = usv::launch_zero_f64(loss_dev, 1, st);
@@ -346,7 +349,7 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
 int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
                      const int32_t *first_rows_dev, void *stream, void *acc_override,
-                     const TileCfg *cfg_override)
+                     const TileCfg *cfg_override, int tri_min_rows)
 {
     if (!vol || !cal || n < 0)
         return USV_ERR_ARG;
@@ -417,7 +420,7 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
                                        cfg);
         else
             e = usv::launch_insert_trilinear(v, img, dtype == USV_F32, nc, H, W, sp.convex,
-                                             cal->r0_mm, cal->dr_mm, st, cfg);
+                                             cal->r0_mm, cal->dr_mm, st, cfg, tri_min_rows);
     }
     if (e == cudaErrorNotSupported)
         return USV_ERR_UNSUPPORTED;
