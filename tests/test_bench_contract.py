@@ -1,0 +1,55 @@
+"""bench.py prints one JSON line with the keys its consumers read: the CPU
+reference arm (the oracle on bounded samples) here, and a short GPU run on
+a 600-frame piece of the sweep on the GPU."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+BASE_KEYS = {"metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+             "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config", "e2e"}
+
+
+def run_bench(*args, timeout=600):
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT,
+                       capture_output=True, text=True, timeout=timeout)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    return json.loads(lines[0])
+
+
+def test_reference_arm_line():
+    d = run_bench("--impl", "reference", "--steps", "2", "--warmup", "1")
+    assert BASE_KEYS <= set(d)
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "frames/s"
+    assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+@pytest.mark.gpu
+def test_gpu_arm_line():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    d = run_bench("--frames", "600", "--steps", "4", "--warmup", "3", "--e2e-steps", "2",
+                  "--stream-seconds", "0", "--no-variants", "--no-cpu-baseline")
+    assert BASE_KEYS <= set(d)
+    assert d["value"] > 0 and d["n_gpus"] == 1 and d["steps"] == 4 and d["warmup"] == 3
+    assert d["gpu_launches"] == 4 * 4
+    rl = d["roofline"]
+    assert rl["bound"] == "hbm" and rl["unit"] == "GB/s" and 0 < rl["frac"] < 2
+    assert abs(rl["frac"] - rl["achieved"] / rl["peak"]) < 1e-9
+    e = d["e2e"]
+    assert e["value"] > 0 and e["h2d_bytes_per_step"] == 600 * 640 * 480 + 600 * 128
+    assert e["d2h_bytes_per_step"] > 0
+    assert set(d["stage_ms"]) == {"insert", "fill", "project", "gaps"}
+    assert d["cuda_graph"]["ms_per_step"] > 0 and d["autotune"]["tile"]
+    clocks = d["clocks"]
+    assert clocks is None or "sm_mhz" in clocks
