@@ -12,9 +12,11 @@
 // q(i) = q(i0) + (i - i0)*d.  The start q(i0) is evaluated in FP64 and split
 // into an integer voxel and a fraction; the fraction and the step d are then
 // carried in Q16.47 fixed point, so after 16 steps the position is still
-// within ~1e-12 voxel of the FP64 value, and both trilinear factors of an
-// axis, f and 1 - f, are formed from exact integers (no cancellation when f
-// is close to 1).  Columns whose step exceeds 256 voxels re-anchor every row.
+// within ~1e-12 voxel of the FP64 value.  The trilinear factors of an axis,
+// f and 1 - f, are formed from that integer fraction with a relative error
+// below 1.5 * 2^-24 each (no cancellation when f is close to 1, and no 64-bit
+// integer-to-float conversion).  Columns whose step exceeds 256 voxels
+// re-anchor every row.
 //
 // GB300 design: a CTA takes a tile of 256 columns x 64 rows of 4 consecutive
 // frames; each thread walks one column through the 64 rows, merging the 8
@@ -62,7 +64,6 @@ struct TriArgs {
 
 constexpr long long kOne47 = 1LL << 47;
 constexpr long long kMask47 = kOne47 - 1;
-constexpr float kInv47 = 7.105427357601002e-15f;  // 2^-47
 constexpr float kWmin = 9.5367431640625e-07f;     // 2^-20
 
 // q (FP64, |q| < 2^30) -> integer voxel floor(q) and Q16.47 fraction
@@ -185,21 +186,27 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
         for (int c = 0; c < 8; ++c)
             cS[c] = cW[c] = 0.0f;
         int cx0 = INT_MIN, cy0 = 0, cz0 = 0;
+        // the next row's sample is loaded while this row is splatted
+        auto sample = [&](int v) {
+            const size_t pi = fbase + (size_t)v * a.W + j;
+            return a.is_f32 ? __ldcs(static_cast<const float *>(a.img) + pi)
+                            : u8_to_float(__ldcs(static_cast<const uint8_t *>(a.img) + pi));
+        };
+        float In = sample(vs);
         for (int v = vs; v < v1; ++v) {
             if (steep && v > vs)
                 for (int ax = 0; ax < 3; ++ax)
                     anchor(base[ax] + (double)(v - vs) * step[ax], i0[ax], fq[ax]);
-            const size_t pi = fbase + (size_t)v * a.W + j;
-            const float I = a.is_f32 ? __ldcs(static_cast<const float *>(a.img) + pi)
-                                     : (float)__ldcs(static_cast<const uint8_t *>(a.img) + pi);
+            const float I = In;
+            if (v + 1 < v1)
+                In = sample(v + 1);
             int ix[3];
             float w1[3], w0[3];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
                 ix[ax] = i0[ax] + (int)(fq[ax] >> 47) - blo[ax];  // box-local (or global)
                 const long long fr = fq[ax] & kMask47;
-                w1[ax] = __ll2float_rn(fr) * kInv47;
-                w0[ax] = __ll2float_rn(kOne47 - fr) * kInv47;
+                tri_factors(fr, w1[ax], w0[ax]);
             }
             if (ix[0] != cx0 || ix[1] != cy0 || ix[2] != cz0) {
                 if (cx0 != INT_MIN)
@@ -231,7 +238,7 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
+__global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
 {
     extern __shared__ float tbox[];  // [kBoxCap] S, then [kBoxCap] W
     __shared__ FrameRec s_rec[kMaxFpc];
@@ -295,10 +302,16 @@ __global__ void __launch_bounds__(kThreads) k_insert_trilinear(TriArgs a)
     const int rv0 = v0, rv1 = v1;
     float *bS = tbox, *bW = tbox + kBoxCap;
     if (mode == 2) {
+        // corner bounds checks only in tiles whose voxel box the grid clips
         const int zero[3] = {0, 0, 0};
-        if (j < j1 && rv0 < rv1)
-            walk<false, true>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
-                              (unsigned)a.ny, (unsigned)a.nz, bS, bW);
+        if (j < j1 && rv0 < rv1) {
+            if (s_check)
+                walk<false, true>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
+                                  (unsigned)a.ny, (unsigned)a.nz, bS, bW);
+            else
+                walk<false, false>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
+                                   (unsigned)a.ny, (unsigned)a.nz, bS, bW);
+        }
         return;
     }
     const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];

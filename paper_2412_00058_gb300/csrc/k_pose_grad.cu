@@ -29,7 +29,6 @@ namespace {
 
 constexpr long long kOne47 = 1LL << 47;
 constexpr long long kMask47 = kOne47 - 1;
-constexpr float kInv47 = 7.105427357601002e-15f;  // 2^-47
 constexpr float kWmin = 9.5367431640625e-07f;     // 2^-20
 
 __device__ __forceinline__ void anchor(double q, int &i0, long long &fq)
@@ -136,7 +135,7 @@ __global__ void __launch_bounds__(256) k_pose_grad(GradArgs a, int tiles_x)
                         anchor(base[ax] + (double)(v - v0) * step[ax], i0[ax], fq[ax]);
                 const size_t pi = ((size_t)f * a.H + v) * a.W + j;
                 const float I = a.is_f32 ? __ldg(static_cast<const float *>(a.img) + pi)
-                                         : (float)__ldg(static_cast<const uint8_t *>(a.img) + pi);
+                                         : u8_to_float(__ldg(static_cast<const uint8_t *>(a.img) + pi));
                 int ix[3];
                 float w1[3], w0[3], rel[3];
 #pragma unroll
@@ -144,8 +143,7 @@ __global__ void __launch_bounds__(256) k_pose_grad(GradArgs a, int tiles_x)
                     const int whole = (int)(fq[ax] >> 47);
                     ix[ax] = i0[ax] + whole;
                     const long long fr = fq[ax] & kMask47;
-                    w1[ax] = __ll2float_rn(fr) * kInv47;
-                    w0[ax] = __ll2float_rn(kOne47 - fr) * kInv47;
+                    tri_factors(fr, w1[ax], w0[ax]);
                     // position relative to the pivot (voxels): (i0s - pivot) + (ix - i0s) + f
                     rel[ax] = off[ax] + (float)(ix[ax] - i0s[ax]) + w1[ax];
                 }

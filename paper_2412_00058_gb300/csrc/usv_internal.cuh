@@ -152,4 +152,33 @@ cudaError_t launch_apply_pose_delta(const double *poses, const double *delta, in
                                     double cz, const double *K, double *out, cudaStream_t st);
 cudaError_t launch_unpack_mask(const Volume &v, uint8_t *dst, cudaStream_t st);
 
+// Trilinear factors (f, 1 - f) of one axis from the Q.47 fraction bits fr
+// (f = fr / 2^47, fr in [0, 2^47)): the smaller of the two, s <= 1/2, is
+// converted correctly rounded -- its 46 bits split into two halves of at
+// most 23 bits, each made exact in the mantissa of a float, joined by one
+// fused multiply-add -- and the larger is 1 - s, rounded.  Both keep a
+// relative error below 1.5 * 2^-24, which a small factor needs (the weighted
+// mean of a voxel reached only by far corners), and the work stays on the
+// integer and FP32 units: a 64-bit integer-to-float conversion runs on the
+// FP64 units.
+__device__ __forceinline__ void tri_factors(long long fr, float &w1, float &w0)
+{
+    const unsigned long long p = (unsigned long long)fr & ((1ull << 47) - 1);
+    const bool upper = (p >> 46) != 0;                              // f >= 1/2
+    const unsigned long long sm = upper ? (1ull << 47) - p : p;     // <= 2^46
+    const unsigned hi = (unsigned)(sm >> 23), lo = (unsigned)sm & 0x7FFFFFu;  // hi <= 2^23
+    const float fh = __int_as_float(0x4B000000 + (int)hi) - 8388608.0f;
+    const float fl = __int_as_float(0x4B000000 + (int)lo) - 8388608.0f;
+    const float small = fmaf(fh, 5.9604644775390625e-08f, fl * 7.105427357601002e-15f);
+    const float big = 1.0f - small;
+    w1 = upper ? big : small;
+    w0 = upper ? small : big;
+}
+
+// A byte as an exact float: 2^23 + b in the mantissa, minus 2^23.
+__device__ __forceinline__ float u8_to_float(unsigned b)
+{
+    return __int_as_float(0x4B000000 | (int)b) - 8388608.0f;
+}
+
 }  // namespace usv
