@@ -23,6 +23,12 @@
 // corner terms of consecutive samples that stay in one cell (about 1.7
 // samples per 0.4 mm cell along a 0.235 mm-step beam) in registers, and
 // sends each cell's terms to HBM with one vector atomic (S, W) per corner.
+// When the beam steps into a face-adjacent cell, the 4 corner voxels the two
+// cells share keep their terms in registers (moved to the new cell's
+// corners), and only the 4 corners left behind are sent: about 40 % fewer
+// atomics on the convex sweep.  This carry costs selects on every cell
+// change; it pays where the atomics miss L2, and a launch can leave it out
+// (the pose-gradient path, whose smaller volume keeps its atomics in L2).
 // A conservative voxel box of the tile (FP64 extremes of the patch -- for a
 // convex fan the depth extreme can sit on the central beam -- plus a
 // one-voxel margin) decides whether the tile touches the grid at all and
@@ -134,15 +140,26 @@ __device__ void patch_box(const TriArgs &a, const FrameRec *r, int j0, int j1, i
 
 // Add one sample's 8 corner terms. Box mode: shared arrays, box-local key;
 // direct mode: HBM vector atomics.
+// Corners of a cell that a step to a face-adjacent cell leaves behind: the
+// step moves by one along the axis of corner bit `abit`, up or down; moving
+// up, the corners with that bit clear stay behind (the others become the
+// new cell's corners with the bit clear), moving down the corners with the
+// bit set.  Any other step (or the end of a column) leaves all 8 behind.
+__device__ __forceinline__ bool left_behind(int c, bool face, int abit, bool up)
+{
+    return !face || (((c & abit) == 0) == up);
+}
+
 template <bool BOX, bool CHECK>
 __device__ __forceinline__ void splat(float *bS, float *bW, float2 *acc, unsigned ex,
                                       unsigned ey, unsigned ez, int lx, int ly, int lz,
-                                      const float (&cS)[8], const float (&cW)[8])
+                                      const float (&cS)[8], const float (&cW)[8],
+                                      bool face = false, int abit = 1, bool up = true)
 {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-        if (cW[c] == 0.0f)
+        if (cW[c] == 0.0f || !left_behind(c, face, abit, up))
             continue;
         const unsigned X = (unsigned)(lx + cx), Y = (unsigned)(ly + cy), Z = (unsigned)(lz + cz);
         if (CHECK && !(X < ex && Y < ey && Z < ez))
@@ -157,7 +174,7 @@ __device__ __forceinline__ void splat(float *bS, float *bW, float2 *acc, unsigne
     }
 }
 
-template <bool BOX, bool CHECK>
+template <bool BOX, bool CHECK, bool CARRY>
 __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int f0, int f1,
                                      int j, int v0, int v1, const int (&blo)[3], unsigned ex,
                                      unsigned ey, unsigned ez, float *bS, float *bW)
@@ -209,11 +226,34 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
                 tri_factors(fr, w1[ax], w0[ax]);
             }
             if (ix[0] != cx0 || ix[1] != cy0 || ix[2] != cz0) {
+                // a step to a face-adjacent cell keeps the 4 corner voxels the
+                // two cells share: their terms move to the new cell's corners
+                // and go out with it; only the corners left behind are sent
+                // (unsigned differences: the first cell's INT_MIN must not overflow)
+                const int dx = (int)((unsigned)ix[0] - (unsigned)cx0);
+                const int dy = (int)((unsigned)ix[1] - (unsigned)cy0);
+                const int dz = (int)((unsigned)ix[2] - (unsigned)cz0);
+                const bool face = CARRY && cx0 != INT_MIN && abs(dx) + abs(dy) + abs(dz) == 1;
+                const int abit = dx != 0 ? 1 : dy != 0 ? 2 : 4;
+                const bool up = dx + dy + dz > 0;
                 if (cx0 != INT_MIN)
-                    splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW);
+                    splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW, face,
+                                      abit, up);
+                float nS[8], nW[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    cS[c] = cW[c] = 0.0f;
+                for (int c = 0; c < 8; ++c) {
+                    // new corner c is old corner c ^ abit when it receives
+                    const bool recv = face && left_behind(c, true, abit, up);
+                    const float s = abit == 1 ? cS[c ^ 1] : abit == 2 ? cS[c ^ 2] : cS[c ^ 4];
+                    const float w = abit == 1 ? cW[c ^ 1] : abit == 2 ? cW[c ^ 2] : cW[c ^ 4];
+                    nS[c] = recv ? s : 0.0f;
+                    nW[c] = recv ? w : 0.0f;
+                }
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    cS[c] = nS[c];
+                    cW[c] = nW[c];
+                }
                 cx0 = ix[0];
                 cy0 = ix[1];
                 cz0 = ix[2];
@@ -238,6 +278,7 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
     }
 }
 
+template <bool CARRY>
 __global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
 {
     extern __shared__ float tbox[];  // [kBoxCap] S, then [kBoxCap] W
@@ -306,10 +347,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
         const int zero[3] = {0, 0, 0};
         if (j < j1 && rv0 < rv1) {
             if (s_check)
-                walk<false, true>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
+                walk<false, true, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
                                   (unsigned)a.ny, (unsigned)a.nz, bS, bW);
             else
-                walk<false, false>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
+                walk<false, false, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
                                    (unsigned)a.ny, (unsigned)a.nz, bS, bW);
         }
         return;
@@ -324,9 +365,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
     const int blo[3] = {s_lo[0], s_lo[1], s_lo[2]};
     if (j < j1 && rv0 < rv1) {
         if (s_check)
-            walk<true, true>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
+            walk<true, true, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
         else
-            walk<true, false>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
+            walk<true, false, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -355,7 +396,7 @@ bool tri_tile_ok(const TileCfg &c)
 
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
                                     int W, int convex, double r0, double dr, cudaStream_t st,
-                                    const TileCfg &cfg, int min_rows)
+                                    const TileCfg &cfg, int min_rows, bool carry)
 {
     if (n <= 0)
         return cudaSuccess;
@@ -400,13 +441,19 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
     if (kUseBox) {
-        const cudaError_t e =
-            prepare_kernel(reinterpret_cast<const void *>(k_insert_trilinear), kBoxBytes);
+        cudaError_t e =
+            prepare_kernel(reinterpret_cast<const void *>(k_insert_trilinear<true>), kBoxBytes);
+        if (e == cudaSuccess)
+            e = prepare_kernel(reinterpret_cast<const void *>(k_insert_trilinear<false>),
+                               kBoxBytes);
         if (e != cudaSuccess)
             return e;
     }
     dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
-    k_insert_trilinear<<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);
+    if (carry)
+        k_insert_trilinear<true><<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);
+    else
+        k_insert_trilinear<false><<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -209,7 +209,8 @@ namespace usv {
 int insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                 int32_t dtype, const double *poses_dev, const usv_calibration *cal,
                 const int32_t *first_rows_dev, void *stream, void *acc_override = nullptr,
-                const TileCfg *cfg_override = nullptr, int tri_min_rows = 8);
+                const TileCfg *cfg_override = nullptr, int tri_min_rows = 8,
+                bool tri_carry = true);
 }
 
 int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
@@ -305,11 +306,14 @@ int usv_pose_loss_grad(usv_volume *vol, const void *images_dev, int32_t n, int32
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     // the gradient kernel recomputes every sample on 64-row tiles, so the
-    // forward splat keeps 64-row tiles (same column anchors, same cells)
+    // forward splat keeps 64-row tiles (same column anchors, same cells);
+    // without the corner carry, which costs more than it saves on the
+    // smaller volumes of pose refinement (their atomics stay in L2)
     int rc = usv_volume_reset(vol, stream);
     if (rc == USV_OK)
         rc = usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream,
-                              nullptr, &usv::kTriTileDefault, usv::kTriTileDefault.tile_h);
+                              nullptr, &usv::kTriTileDefault, usv::kTriTileDefault.tile_h,
+                              false);
     if (rc != USV_OK)
         return rc;
     cudaError_t e = usv::launch_zero_f64(loss_dev, 1, st);
@@ -349,7 +353,7 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
 int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
                      const int32_t *first_rows_dev, void *stream, void *acc_override,
-                     const TileCfg *cfg_override, int tri_min_rows)
+                     const TileCfg *cfg_override, int tri_min_rows, bool tri_carry)
 {
     if (!vol || !cal || n < 0)
         return USV_ERR_ARG;
@@ -420,7 +424,8 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
                                        cfg);
         else
             e = usv::launch_insert_trilinear(v, img, dtype == USV_F32, nc, H, W, sp.convex,
-                                             cal->r0_mm, cal->dr_mm, st, cfg, tri_min_rows);
+                                             cal->r0_mm, cal->dr_mm, st, cfg, tri_min_rows,
+                                             tri_carry);
     }
     if (e == cudaErrorNotSupported)
         return USV_ERR_UNSUPPORTED;

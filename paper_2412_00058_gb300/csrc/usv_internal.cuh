@@ -126,10 +126,12 @@ cudaError_t launch_bone_rows_alg2(const uint8_t *img, int n, int H, int W, int f
 cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H, int W,
                               cudaStream_t st, const TileCfg &cfg = kPnnTileDefault);
 // min_rows: the fewest rows per tile a small batch may be cut to (the tile
-// rows anchor each column's walk)
+// rows anchor each column's walk); carry: keep the corner terms two
+// face-adjacent cells share in registers across the step
 cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32, int n, int H,
                                     int W, int convex, double r0, double dr, cudaStream_t st,
-                                    const TileCfg &cfg = kTriTileDefault, int min_rows = 8);
+                                    const TileCfg &cfg = kTriTileDefault, int min_rows = 8,
+                                    bool carry = true);
 // fill / project a region: voxels [lo, hi) (clipped to the grid; the fill
 // needs lo[0] a multiple of 32), columns [rlo, rhi)
 // clear: accumulators to zero in the pass; withhold: test hook (a plane whose
