@@ -239,20 +239,29 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
                 if (cx0 != INT_MIN)
                     splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW, face,
                                       abit, up);
-                float nS[8], nW[8];
+                // new corner c is old corner c ^ abit when it receives: 0/1
+                // masks and multiply-adds (exact: one term is kept, the others
+                // are multiplied by zero) keep this off the integer pipe
+                if constexpr (CARRY) {
+                    const float mx = face && abit == 1 ? 1.0f : 0.0f;
+                    const float my = face && abit == 2 ? 1.0f : 0.0f;
+                    const float mz = face && abit == 4 ? 1.0f : 0.0f;
+                    float nS[8], nW[8];
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    // new corner c is old corner c ^ abit when it receives
-                    const bool recv = face && left_behind(c, true, abit, up);
-                    const float s = abit == 1 ? cS[c ^ 1] : abit == 2 ? cS[c ^ 2] : cS[c ^ 4];
-                    const float w = abit == 1 ? cW[c ^ 1] : abit == 2 ? cW[c ^ 2] : cW[c ^ 4];
-                    nS[c] = recv ? s : 0.0f;
-                    nW[c] = recv ? w : 0.0f;
-                }
+                    for (int c = 0; c < 8; ++c) {
+                        const float rf = left_behind(c, true, abit, up) ? 1.0f : 0.0f;
+                        nS[c] = rf * fmaf(mx, cS[c ^ 1], fmaf(my, cS[c ^ 2], mz * cS[c ^ 4]));
+                        nW[c] = rf * fmaf(mx, cW[c ^ 1], fmaf(my, cW[c ^ 2], mz * cW[c ^ 4]));
+                    }
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    cS[c] = nS[c];
-                    cW[c] = nW[c];
+                    for (int c = 0; c < 8; ++c) {
+                        cS[c] = nS[c];
+                        cW[c] = nW[c];
+                    }
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        cS[c] = cW[c] = 0.0f;
                 }
                 cx0 = ix[0];
                 cy0 = ix[1];
