@@ -243,15 +243,22 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
                 // masks and multiply-adds (exact: one term is kept, the others
                 // are multiplied by zero) keep this off the integer pipe
                 if constexpr (CARRY) {
-                    const float mx = face && abit == 1 ? 1.0f : 0.0f;
-                    const float my = face && abit == 2 ? 1.0f : 0.0f;
-                    const float mz = face && abit == 4 ? 1.0f : 0.0f;
+                    // receiving along axis bit b: the corners with b clear
+                    // on a step up, with b set on a step down -- fixed per
+                    // corner, so one mask per axis and direction
+                    const float xl = face && abit == 1 && up ? 1.0f : 0.0f;
+                    const float xh = face && abit == 1 && !up ? 1.0f : 0.0f;
+                    const float yl = face && abit == 2 && up ? 1.0f : 0.0f;
+                    const float yh = face && abit == 2 && !up ? 1.0f : 0.0f;
+                    const float zl = face && abit == 4 && up ? 1.0f : 0.0f;
+                    const float zh = face && abit == 4 && !up ? 1.0f : 0.0f;
                     float nS[8], nW[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        const float rf = left_behind(c, true, abit, up) ? 1.0f : 0.0f;
-                        nS[c] = rf * fmaf(mx, cS[c ^ 1], fmaf(my, cS[c ^ 2], mz * cS[c ^ 4]));
-                        nW[c] = rf * fmaf(mx, cW[c ^ 1], fmaf(my, cW[c ^ 2], mz * cW[c ^ 4]));
+                        const float kx = (c & 1) ? xh : xl, ky = (c & 2) ? yh : yl;
+                        const float kz = (c & 4) ? zh : zl;
+                        nS[c] = fmaf(kx, cS[c ^ 1], fmaf(ky, cS[c ^ 2], kz * cS[c ^ 4]));
+                        nW[c] = fmaf(kx, cW[c ^ 1], fmaf(ky, cW[c ^ 2], kz * cW[c ^ 4]));
                     }
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
