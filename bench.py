@@ -14,14 +14,17 @@ Prints one JSON line (rank 0):
   value      frames/s of the whole job (all ranks), CUDA-event timed
   e2e        the same metric through the public API from pinned HOST buffers,
              frames streamed host->device in 300-frame batches overlapped
-             with insertion, projection read back every step
+             with insertion, poses passed from host memory, projection read
+             back every step; with the host link measured in the same run
   roofline   the dominant kernel (insertion): algorithmic bytes / its event-
              timed launch duration vs the measured HBM copy bandwidth
-  cpu_baseline  the CPU oracle on a bounded sample of the same sweep
+  cpu_baseline  the CPU oracle on the whole sweep, on all host cores (and on
+             one thread)
   clocks     nvidia-smi SM clocks / throttle reasons sampled while timing
 
 --impl reference times the CPU oracle (the only reference: the paper
-publishes no code) on the same metric.  Multi-GPU: replicas only -- every
+publishes no code) on the same metric: the whole sweep every step, on all
+host cores.  Multi-GPU: replicas only -- every
 rank reconstructs its own sweep with no collective in the data path; the
 barrier and a MAX all-reduce of the elapsed time bracket the timed region.
 """
@@ -177,6 +180,31 @@ class ClockSampler:
                 "samples": len(inside)}
 
 
+# ---------------------------------------------------------------- host placement
+
+def gpu_local_cpus(index: int) -> set:
+    """Host CPUs on the GPU's own NUMA node (from the PCI device's
+    local_cpulist), intersected with this process's CPUs; empty if unknown."""
+    try:
+        bus = subprocess.run(["nvidia-smi", "-i", str(index), "--query-gpu=pci.bus_id",
+                              "--format=csv,noheader"], capture_output=True, text=True,
+                             timeout=20).stdout.strip().lower()
+        dom, rest = bus.split(":", 1)
+        path = f"/sys/bus/pci/devices/{int(dom, 16):04x}:{rest}/local_cpulist"
+        with open(path) as f:
+            spec = f.read().strip()
+    except (OSError, ValueError, subprocess.SubprocessError):
+        return set()
+    cpus = set()
+    for part in spec.split(","):
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus & os.sched_getaffinity(0)
+
+
 # ---------------------------------------------------------------- peaks
 
 def measured_peaks():
@@ -229,59 +257,41 @@ def sweep_workload(frames: int = 3600):
 # ---------------------------------------------------------------- CPU oracle
 
 def oracle_accumulators(w):
-    """Zeroed full-volume oracle accumulators [sums, counts, box], every page
-    written once here, so that no timed call pays for first-touch page
-    faults."""
+    """Full-volume oracle accumulators (sums, counts), every page written once
+    here, so that no timed call pays for first-touch page faults."""
     import numpy as np
     nx, ny, nz = w.grid
     s = np.empty((nz, ny, nx), np.uint64)
     c = np.empty((nz, ny, nx), np.uint32)
     s.fill(0)
     c.fill(0)
-    return [s, c, None]
+    return s, c
 
 
-def oracle_sweep_seconds(w, frac: float, rng_offset: int = 0, acc=None):
-    """Time the oracle on a bounded sample of the sweep and scale it to the
-    whole sweep: insert `frac` of the frames (from rng_offset) into the full
-    volume, then fill + project the y-slab those frames cover; the insert
-    time is scaled by 1/frac, the fill/project time by ny/slab.  The
-    accumulators are allocated and zeroed outside the timed calls (acc).
-    Returns (seconds per full sweep, description, CPU seconds spent).
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0))
 
-    `acc` = [sums, counts, box]: box is the voxel box the previous call's
-    frames could touch, the only part that has to be zeroed again."""
-    import numpy as np
+
+def oracle_sweep_seconds(w, threads: int = 1, acc=None):
+    """Time the oracle on the whole sweep: every frame inserted into the full
+    volume, then fill and projection of the whole volume, on `threads` host
+    threads (1: the plain single-thread loops).  The accumulators are zeroed
+    before the timed calls.  Returns (seconds, threads used)."""
     import oracle
-    from paper_2412_00058_gb300.stream import frames_voxel_box
-    n = w.n
-    k = max(1, int(round(n * frac)))
-    f0 = min(n - k, rng_offset)
-    nx, ny, nz = w.grid
-    if acc is None:
-        acc = oracle_accumulators(w)
-    s, c, box = acc
-    if box is not None:
-        (x0, y0b, z0), (x1, y1b, z1) = box
-        s[z0:z1, y0b:y1b, x0:x1] = 0
-        c[z0:z1, y0b:y1b, x0:x1] = 0
-    acc[2] = frames_voxel_box(w, w.poses[f0:f0 + k])
-    t0 = time.perf_counter()
-    oracle.insert_pnn(w.grid, w.images[f0:f0 + k], w.poses[f0:f0 + k], w.calib, w.sx, w.sy,
-                      w.spacing, w.origin, sum_=s, cnt=c)
-    t_ins = time.perf_counter() - t0
-    rows = max(3, int(round(ny * frac)))
-    y0 = int(np.clip(np.median(w.poses[f0:f0 + k, 1, 3]) / w.spacing[1] - rows / 2, 0, ny - rows))
-    ss = np.ascontiguousarray(s[:, y0:y0 + rows, :])
-    cc = np.ascontiguousarray(c[:, y0:y0 + rows, :])
-    t0 = time.perf_counter()
-    val, has = oracle.fill_pnn(ss, cc)
-    oracle.project_u8(val, has, *w.band)
-    t_fp = time.perf_counter() - t0
-    sweep = t_ins * (n / k) + t_fp * (ny / rows)
-    desc = (f"oracle insert of frames [{f0},{f0 + k}) of {n} (x{n / k:.1f}) + fill/project of "
-            f"y-slab [{y0},{y0 + rows}) of {ny} (x{ny / rows:.1f}); single thread")
-    return sweep, desc, t_ins + t_fp
+    s, c = acc if acc is not None else oracle_accumulators(w)
+    s.fill(0)
+    c.fill(0)
+    used = oracle.set_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        oracle.insert_pnn(w.grid, w.images, w.poses, w.calib, w.sx, w.sy, w.spacing, w.origin,
+                          sum_=s, cnt=c)
+        val, has = oracle.fill_pnn(s, c)
+        oracle.project_u8(val, has, *w.band)
+        t = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(1)
+    return t, used
 
 
 def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
@@ -357,37 +367,36 @@ def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
 
 
 def run_reference(args):
+    """The oracle (the only reference: the paper publishes no code) as it
+    stands, on all host cores, over the whole sweep every step."""
     rank, _, world = dist_env()
     if rank != 0:
         return 0
     from paper_2412_00058_gb300 import synth
     import oracle
     oracle.build()
-    import numpy as np
-    w = synth.whole_spine()
-    nx, ny, nz = w.grid
+    w = synth.whole_spine() if args.frames >= 3600 else sweep_workload(args.frames)
     acc = oracle_accumulators(w)
-    # 12 frames per step (~50 ms of oracle work), fewer only for runs so
-    # long that the steps would pass about two minutes
-    per_step = max(1, min(12, int(120.0 / (max(args.steps + args.warmup, 1) * 0.0045))))
-    frac = per_step / w.n
-    for i in range(args.warmup):
-        oracle_sweep_seconds(w, frac, rng_offset=(i * 97) % w.n, acc=acc)
-    sweeps, cpu_s = [], 0.0
-    for i in range(args.steps):
-        s, desc, t = oracle_sweep_seconds(w, frac, rng_offset=(i * 389 + 1234) % w.n, acc=acc)
-        sweeps.append(s)
-        cpu_s += t
-    sweep = statistics.mean(sweeps)
-    value = w.n / sweep
+    cores = host_cores()
+    for _ in range(args.warmup):
+        oracle_sweep_seconds(w, cores, acc)
+    times, used = [], 1
+    for _ in range(args.steps):
+        t, used = oracle_sweep_seconds(w, cores, acc)
+        times.append(t)
+    total = sum(times)
+    value = w.n * len(times) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": sweep * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": total / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": f"per step: {desc}; {cpu_s:.1f} s of CPU work in total"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": used, "kind": "oracle",
+                         "sample": f"the whole sweep every step ({w.n} frames inserted into the "
+                                   f"full {w.grid[0]}x{w.grid[1]}x{w.grid[2]} volume, fill and "
+                                   f"projection of the whole volume), accumulators zeroed "
+                                   f"before each step outside its timing; {used} threads"},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -552,27 +561,49 @@ def run_gpu(args):
     achieved = ins_bytes / (ins_ms / 1e3) / 1e9
     fill_bytes = nvox * (8 + 1) + nz * ny * ((nx + 31) // 32) * 4
     proj_bytes = (hi - lo) * ny * (nx + ((nx + 31) // 32) * 4 / 1) + ny * nx * 6
-    clear_bytes = nvox * 8  # zeros for the next sweep, written by the fill
-    step_bytes = clear_bytes + ins_bytes + fill_bytes + proj_bytes
+    # zeros for the next sweep, written by the fill: work of every step, but
+    # not bytes the method moves, so not counted in the fractions
+    clear_bytes = nvox * 8
+    step_bytes = ins_bytes + fill_bytes + proj_bytes
 
     # ---- end to end through the public API from pinned host memory: every
     # step copies its sweep host->device (12 batches of 300 frames on a copy
-    # stream, each batch inserted as soon as it has landed) and reads its
-    # projection back.  Two device frame buffers let the next sweep's copies
-    # start while this sweep is still being filled and projected; the host
-    # waits once, after the last step.
+    # stream, each batch inserted as soon as it has landed, its poses passed
+    # from host memory: the library stages them) and reads its projection
+    # back.  Two device frame buffers let the next sweep's copies start while
+    # this sweep is still being filled and projected; the host waits once,
+    # after the last step.  The pinned buffers are placed on the GPU's own
+    # NUMA node, and the host link is measured in the same run (one 1.1 GB
+    # pinned host->device copy, best of 3).
     e2e = None
     if args.e2e_steps > 0:
-        h_imgs = torch.from_numpy(w.images).pin_memory()
-        h_poses = torch.from_numpy(w.poses).pin_memory()
-        h_out = [torch.empty((ny, nx), dtype=torch.float32).pin_memory() for _ in range(2)]
-        h_cnt = [torch.empty((ny, nx), dtype=torch.int16).pin_memory() for _ in range(2)]
+        local = gpu_local_cpus(dev.index)
+        prev_aff = os.sched_getaffinity(0)
+        if local:
+            os.sched_setaffinity(0, local)   # first touch of the pinned pages: local node
+        try:
+            h_imgs = torch.from_numpy(w.images).pin_memory()
+            h_poses = torch.from_numpy(w.poses).pin_memory()
+            h_out = [torch.empty((ny, nx), dtype=torch.float32).pin_memory() for _ in range(2)]
+            h_cnt = [torch.empty((ny, nx), dtype=torch.int16).pin_memory() for _ in range(2)]
+        finally:
+            os.sched_setaffinity(0, prev_aff)
         d_imgs = [imgs, torch.empty_like(imgs)]
-        d_poses = [poses, torch.empty_like(poses)]
         copy_stream = torch.cuda.Stream(dev)
         batch = 300
         bounds = [(b, min(w.n, b + batch)) for b in range(0, w.n, batch)]
         freed = [None, None]  # per buffer: the inserts that last read it
+
+        # the host link: the same bytes in one pinned host->device copy
+        link = []
+        le0, le1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(3):
+            le0.record(copy_stream)
+            d_imgs[1].copy_(h_imgs, non_blocking=True)
+            le1.record(copy_stream)
+            le1.synchronize()
+            link.append(h_imgs.numel() / (le0.elapsed_time(le1) / 1e3) / 1e9)
+        link_gbs = max(link)
 
         def e2e_steps(k_steps):
             for k in range(k_steps):
@@ -583,13 +614,12 @@ def run_gpu(args):
                         copy_stream.wait_event(freed[buf])
                     for b0, b1 in bounds:
                         d_imgs[buf][b0:b1].copy_(h_imgs[b0:b1], non_blocking=True)
-                        d_poses[buf][b0:b1].copy_(h_poses[b0:b1], non_blocking=True)
                         e = torch.cuda.Event()
                         e.record(copy_stream)
                         landed.append(e)
                 for (b0, b1), e in zip(bounds, landed):
                     stream.wait_event(e)
-                    vol.insert(d_imgs[buf][b0:b1], d_poses[buf][b0:b1], cal, stream)
+                    vol.insert(d_imgs[buf][b0:b1], h_poses[b0:b1], cal, stream)
                 freed[buf] = torch.cuda.Event()
                 freed[buf].record(stream)
                 vol.fill_and_clear(stream)
@@ -606,13 +636,21 @@ def run_gpu(args):
         last = e2e_steps(args.e2e_steps)
         t_e = max_over_ranks(time.perf_counter() - t_e0, dev)
         assert np.array_equal(h_out[last].numpy(), out.cpu().numpy())
+        frames_gbs = w.images.nbytes * args.e2e_steps / t_e / 1e9
         e2e = {"value": w.n * world * args.e2e_steps / t_e, "unit": "frames/s",
                "h2d_bytes_per_step": int(w.images.nbytes + w.poses.nbytes),
                "d2h_bytes_per_step": int(h_out[0].numel() * 4 + h_cnt[0].numel() * 2),
                "ms_per_step": t_e / args.e2e_steps * 1e3,
+               "host_link": {"h2d_gbs": link_gbs, "frames_gbs": frames_gbs,
+                             "frac": frames_gbs / link_gbs,
+                             "pinned_on_cpus": f"{len(local)} GPU-local cpus" if local
+                             else "default placement (GPU-local cpus not found)",
+                             "what": "one 1.1 GB pinned host->device copy of the same frames, "
+                                     "best of 3, measured in this run"},
                "pipeline": f"{len(bounds)} batches of {batch} frames, H2D on a copy stream "
-                           "overlapped with insertion; two device frame buffers, so the next "
-                           "sweep's copies overlap this sweep's fill and projection"}
+                           "overlapped with insertion, host poses staged by the library; two "
+                           "device frame buffers, so the next sweep's copies overlap this "
+                           "sweep's fill and projection"}
 
     # ---- streaming: four concurrent sessions, frame-to-render latency
     streaming = None
@@ -659,17 +697,24 @@ def run_gpu(args):
     if not args.no_variants and world == 1:
         variants = measure_variants(dev, frames=args.variant_frames, tune=not args.no_tune)
 
-    # ---- CPU oracle on a bounded sample (rank 0, one GPU only)
+    # ---- CPU oracle (rank 0, one GPU only): the whole sweep on one thread
+    # and on every host core, each run twice (about 20 s of CPU work)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         oracle.build()
-        # the whole sweep, twice (about 15 s of single-thread CPU work), no scaling
-        runs = [oracle_sweep_seconds(w, 1.0) for _ in range(2)]
-        sweep_s = sum(r[0] for r in runs) / len(runs)
-        cpu_work = sum(r[2] for r in runs)
-        cpu = {"value": w.n / sweep_s, "unit": "frames/s", "cores": 1, "kind": "oracle",
-               "sample": f"{runs[0][1]}; run twice, mean; {cpu_work:.1f} s of CPU work"}
+        acc = oracle_accumulators(w)
+        one = [oracle_sweep_seconds(w, 1, acc)[0] for _ in range(2)]
+        multi = [oracle_sweep_seconds(w, host_cores(), acc) for _ in range(2)]
+        used = multi[0][1]
+        t_all = sum(t for t, _ in multi) / len(multi)
+        del acc
+        cpu = {"value": w.n / t_all, "unit": "frames/s", "cores": used, "kind": "oracle",
+               "sample": f"the whole sweep ({w.n} frames into the full volume, fill and "
+                         f"projection of the whole volume) on {used} host threads, run twice, "
+                         f"mean",
+               "single_thread": {"value": w.n / (sum(one) / len(one)), "unit": "frames/s",
+                                 "cores": 1, "sample": "the same sweep on one thread, twice"}}
 
     clocks = sampler.summary(t0, t1) if sampler else None
     # the insertion kernel against the instruction-issue roofline: 4 warp
@@ -706,15 +751,23 @@ def run_gpu(args):
                          "algorithmic_bytes": ins_bytes, "peak_kind": peak_kind},
             "issue_roofline": issue,
             "stage_rooflines": {
-                "fill_and_clear": {"algorithmic_bytes": fill_bytes + clear_bytes,
-                                   "achieved_gbs": (fill_bytes + clear_bytes) / (fill_ms / 1e3) / 1e9,
-                                   "frac": (fill_bytes + clear_bytes) / (fill_ms / 1e3) / 1e9 / peak},
+                "fill_and_clear": {"algorithmic_bytes": fill_bytes,
+                                   "achieved_gbs": fill_bytes / (fill_ms / 1e3) / 1e9,
+                                   "frac": fill_bytes / (fill_ms / 1e3) / 1e9 / peak,
+                                   "clear_bytes": clear_bytes,
+                                   "raw_gbs_with_clear": (fill_bytes + clear_bytes) /
+                                                         (fill_ms / 1e3) / 1e9},
                 "project": {"algorithmic_bytes": proj_bytes,
                             "achieved_gbs": proj_bytes / (proj_ms / 1e3) / 1e9,
                             "frac": proj_bytes / (proj_ms / 1e3) / 1e9 / peak}},
             "pipeline_roofline": {"algorithmic_bytes_per_step": step_bytes,
                                   "achieved_gbs": step_bytes / (ms_per_step / 1e3) / 1e9,
-                                  "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak},
+                                  "frac": step_bytes / (ms_per_step / 1e3) / 1e9 / peak,
+                                  "bytes": "insert (frames + 16 B per touched voxel) + fill "
+                                           "(8 + 1 + 1/8 B per voxel) + projection; the "
+                                           "zeros the fill writes for the next sweep are "
+                                           "not counted",
+                                  "clear_bytes_per_step": clear_bytes},
             "touched_voxels": touched, "pixel_hits": hits,
             "p50_frame_to_render_ms": streaming["p50_ms"] if streaming else None,
             "p99_frame_to_render_ms": streaming["p99_ms"] if streaming else None,

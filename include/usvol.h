@@ -26,8 +26,10 @@
  *    cudaStream_t; NULL = legacy default stream).  Device-side conditions
  *    (skipped frames, saturated voxels) are reported by usv_status().
  *  - Pointers named *_dev are device pointers owned by the caller; they must
- *    stay valid until the stream has passed the call.  The library never
- *    allocates device memory: the volume lives in caller-provided storage.
+ *    stay valid until the stream has passed the call.  Pointers named *_host
+ *    are host memory read during the call only.  The library never
+ *    allocates device memory: the volume lives in caller-provided storage
+ *    (each volume handle owns 2 MB of pinned host memory for staging poses).
  *  - Return value: USV_OK (0) or a negative USV_ERR_* code.  Argument errors
  *    are detected on the host before anything is launched.
  *  - A usv_volume is not thread-safe; use it from one host thread / stream.
@@ -42,7 +44,7 @@
 extern "C" {
 #endif
 
-#define USVOL_ABI_VERSION 1
+#define USVOL_ABI_VERSION 2
 
 /* ---- return codes ---- */
 #define USV_OK 0
@@ -132,7 +134,15 @@ int usv_volume_reset(usv_volume *vol, void *stream);
  * reconstruction of the newly acquired frames only, on top of what the
  * volume already holds -- the paper's incremental method).
  *   images_dev  [n][H][W] uint8 (USV_U8) or float32 (USV_F32), C-order.
- *   poses_dev   [n][16] float64 probe->world matrices, 8-byte aligned.
+ *   poses_host  [n][16] float64 probe->world matrices in host memory (the
+ *               tracker's output, Sec. II.B), row-major; read during the
+ *               call: they are copied into the volume's pinned staging ring
+ *               (2 MB, allocated by usv_volume_create) and from there to the
+ *               device on `stream`.  The call waits on the host only when
+ *               the ring is still held by copies the device has not done yet
+ *               (more than 2 MB of poses in flight).  Not allowed while
+ *               `stream` is being captured into a CUDA graph
+ *               (USV_ERR_UNSUPPORTED): capture usv_insert_frames_dev().
  *   cal         host struct, read during the call only.
  * USV_PNN: every pixel goes to its nearest voxel; with the per-frame map
  *   q(u,v) = C + u*A + v*B quantised to Q31.32 (each of the nine values
@@ -144,21 +154,51 @@ int usv_volume_reset(usv_volume *vol, void *stream);
  *   Needs USV_U8 and USV_LINEAR.
  * USV_TRILINEAR: each sample spreads I over its 8 neighbouring voxels with
  *   trilinear weights (weights < 2^-20 and out-of-grid corners dropped),
- *   FP32 accumulation.  USV_U8 or USV_F32; USV_LINEAR or USV_CONVEX.
+ *   FP32 accumulation.  USV_U8 or USV_F32; USV_LINEAR or USV_CONVEX.  A
+ *   USV_F32 sample is inserted only if it is finite with |I| <= 2^64; a NaN,
+ *   an infinity or a larger magnitude counts as a missing sample (no weight
+ *   anywhere), so it cannot spread into other voxels.
  * A frame whose pose is not affine (bottom row != 0 0 0 1), not finite, or
  * maps outside +-2^29 voxels (|A|,|B| >= 2^14 per step) is skipped and sets
  * USV_STATUS_BAD_POSE.  Limits: 0 <= n, 1 <= H, W <= 32768.
  * ---------------------------------------------------------------------- */
 int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
-                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                      int32_t dtype, const double *poses_host, const usv_calibration *cal,
                       void *stream);
+
+/* usv_insert_frames with the poses already in device memory (poses_dev
+ * [n][16] float64, 8-byte aligned, read by the device when the stream gets
+ * there): no host staging, so it can be captured into a CUDA graph.  Same
+ * result, arguments and errors otherwise. */
+int usv_insert_frames_dev(usv_volume *vol, const void *images_dev, int32_t n, int32_t H,
+                          int32_t W, int32_t dtype, const double *poses_dev,
+                          const usv_calibration *cal, void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_frames_voxel_box -- the voxel box [lo, hi) (x, y, z; half-open,
+ * clipped to the grid) that holds every voxel the given frames can write,
+ * nearest voxel or trilinear corner, widened by `margin` >= 0 voxels on
+ * every side: the region that changes when they are inserted (the paper
+ * re-processes only the areas that need updating, Sec. II.C).  Pass it,
+ * widened by one more voxel, to usv_fill_holes_region() and its x-y part to
+ * usv_project_depth_band_region().  Computed on the host in FP64 from the
+ * frames' in-plane corners (the map is affine in the image plane), with one
+ * voxel of slack for rounding; frames the insertion would skip (pose not
+ * affine or not finite) are ignored; with none left the box is empty
+ * (lo = hi = 0).  grid, spacing_mm, origin_mm as for usv_volume_create()
+ * (no volume needed, no device work); poses_host [n][16] as for
+ * usv_insert_frames().
+ * ---------------------------------------------------------------------- */
+int usv_frames_voxel_box(usv_grid grid, const double spacing_mm[3], const double origin_mm[3],
+                         const double *poses_host, int32_t n, int32_t H, int32_t W,
+                         const usv_calibration *cal, int32_t margin, int32_t lo[3], int32_t hi[3]);
 
 /* ------------------------------------------------------------------------
  * Tissue segmentation by depth of cut (the paper's Algorithms 1 and 2,
  * Sec. II.D): rows of a frame above its "depth of cut" -- the superficial
  * tissue over the bone -- are not inserted (Alg. 1 step 5, Alg. 2 step 4).
  *
- * usv_insert_frames_cut -- usv_insert_frames with first_row_dev[n] (device
+ * usv_insert_frames_cut -- usv_insert_frames_dev with first_row_dev[n] (device
  *   int32): rows v < first_row_dev[f] of frame f are cut away (for a convex
  *   probe: radial samples i < first_row).  Negative values keep every row.
  *
@@ -250,7 +290,7 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
  * insertion kernel whose thread blocks walk the jobs' tiles of frames.
  * Every job: a USV_PNN volume, USV_U8 frames, a USV_LINEAR calibration,
  * 0 <= n <= 4096 frames; the arguments of a job mean what they mean for
- * usv_insert_frames().  All volumes on one device, each in at most one job,
+ * usv_insert_frames_dev().  All volumes on one device, each in at most one job,
  * at most 32 jobs (USV_ERR_RANGE beyond; USV_ERR_ARG for a repeated volume
  * or volumes on different devices; USV_ERR_UNSUPPORTED for other modes or
  * geometries).  A volume's tile shape (usv_set_tile_config, usv_tune_insert)
@@ -282,7 +322,7 @@ int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *str
  *   scratch_dev    device, 16-byte aligned, >= 8 * nx * ny * nz bytes
  *   best_out       the chosen shape (may be NULL)
  *   best_ms_out    its insertion time in ms for the frames tried (may be NULL)
- * Arguments and errors as usv_insert_frames(), plus USV_ERR_NOMEM for a
+ * Arguments and errors as usv_insert_frames_dev(), plus USV_ERR_NOMEM for a
  * short scratch.
  * usv_set_tile_config sets the shape for frames of H x W (cfg NULL: back to
  * the default); USV_ERR_RANGE if invalid for the volume's mode, at most 8
@@ -378,7 +418,7 @@ int usv_volume_write_accum(usv_volume *vol, const void *src_dev, void *stream);
  *               high 32 bits count, the USV_READ_ACCUM layout), owned by the
  *               caller, 8-byte aligned; zero it to start a scan.
  *   grid, spacing_mm, origin_mm   as for usv_volume_create().
- *   images_dev, n, H, W, poses_dev, cal   as for usv_insert_frames(),
+ *   images_dev, n, H, W, poses_dev, cal   as for usv_insert_frames_dev(),
  *               uint8 frames of a linear probe.
  *   status_dev  optional device word: USV_STATUS_* bits are OR-ed into it
  *               (clear it first); NULL: not reported.
@@ -386,8 +426,9 @@ int usv_volume_write_accum(usv_volume *vol, const void *src_dev, void *stream);
  * library sized for USV_NOALLOC_MAX_FRAMES frames (about 160 KB that every
  * GPU which loads the library keeps until the process exits); n beyond that
  * returns USV_ERR_RANGE -- split larger batches.  The first call on each
- * device looks up the array's device address; make that first call before
- * any stream capture.  All calls on one device share the array, so calls
+ * device (and the first after the device's context was reset) looks up the
+ * array's device address and the device's SM count; make that first call
+ * before any stream capture.  All calls on one device share the array, so calls
  * that overlap on the GPU (unordered streams) race: order them on one
  * stream.  Nothing in the array has to start at zero: every call writes the
  * records it reads.  Asynchronous on `stream` like the other calls.
@@ -410,6 +451,19 @@ int usv_insert_pnn_noalloc(uint64_t *accum_dev, usv_grid grid, const double spac
  * even nx), the only one that waits on the device.
  * ---------------------------------------------------------------------- */
 int usv_test_fill_wait_timeout(usv_volume *vol, int32_t plane, void *stream);
+
+/* ------------------------------------------------------------------------
+ * usv_test_insert_trilinear_carry -- for testing only (no counterpart in the
+ * paper).  usv_insert_frames_dev() on a USV_TRILINEAR volume with the register
+ * carry of shared corner terms between face-adjacent cells switched on
+ * (carry != 0, what usv_insert_frames() does) or off (what the pose-gradient
+ * path does), so that both forms of the kernel can be checked against the
+ * oracle on the same frames.  Same arguments and errors as
+ * usv_insert_frames_dev(); USV_ERR_UNSUPPORTED for a USV_PNN volume.
+ * ---------------------------------------------------------------------- */
+int usv_test_insert_trilinear_carry(usv_volume *vol, const void *images_dev, int32_t n,
+                                    int32_t H, int32_t W, int32_t dtype, const double *poses_dev,
+                                    const usv_calibration *cal, int32_t carry, void *stream);
 
 /* Synchronise `stream`, then return the device status bits (>= 0) and clear
  * them, or a negative USV_ERR_* code. */

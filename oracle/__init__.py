@@ -36,12 +36,17 @@ CFLAGS = ["-O2", "-std=c11", "-Wall", "-ffp-contract=off", "-fPIC", "-shared"]
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/liboracle.so (if stale)."""
+    """Compile the oracle with gcc into oracle/liboracle.so (if stale), with
+    OpenMP for its multi-core forms where the compiler has it (without it
+    they run on one thread)."""
     stale = (not os.path.exists(_LIB) or
              os.path.getmtime(_LIB) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
     if force or stale:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
+        r = subprocess.run(["gcc", *CFLAGS, "-fopenmp", _SRC, "-o", tmp, "-lm"],
+                           capture_output=True, text=True)
+        if r.returncode != 0:
+            subprocess.run(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"], check=True)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -60,6 +65,10 @@ def _load():
             P = ctypes.c_void_p
             I = ctypes.c_int
             D = ctypes.c_double
+            lib.ora_set_threads.argtypes = [I]
+            lib.ora_set_threads.restype = I
+            lib.ora_insert_pnn_rows_mt.argtypes = [P, P, I, I, I, P, I, I, I, P, P, D, D, P, P, P]
+            lib.ora_insert_pnn_rows_mt.restype = ctypes.c_int64
             lib.ora_round_half_away.argtypes = [D]
             lib.ora_round_half_away.restype = ctypes.c_int64
             lib.ora_frame_affine_q32.argtypes = [P, P, D, D, P, P, P]
@@ -102,6 +111,18 @@ def _f64(a, shape=None) -> np.ndarray:
     return a
 
 
+_threads = 1
+
+
+def set_threads(n: int) -> int:
+    """Host threads for the nearest-neighbour insertion, fill and projection
+    (1: the plain single-thread loops).  Returns the count in effect (1 if
+    the oracle was built without OpenMP)."""
+    global _threads
+    _threads = int(_load().ora_set_threads(int(n)))
+    return _threads
+
+
 def round_half_away(x: float) -> int:
     return int(_load().ora_round_half_away(float(x)))
 
@@ -128,10 +149,10 @@ def insert_pnn(grid, images, poses, calib, sx, sy, spacing, origin, sum_=None, c
         cnt = np.zeros((nz, ny, nx), dtype=np.uint32)
     poses = _f64(poses, (n, 16))
     fr = None if first_rows is None else np.ascontiguousarray(first_rows, dtype=np.int32)
-    sk = _load().ora_insert_pnn_rows(_ptr(sum_), _ptr(cnt), nx, ny, nz, _ptr(images), n, H, W,
-                                     _ptr(poses), _ptr(_f64(calib, 16)), float(sx), float(sy),
-                                     _ptr(_f64(spacing, 3)), _ptr(_f64(origin, 3)),
-                                     _ptr(fr) if fr is not None else None)
+    fn = _load().ora_insert_pnn_rows_mt if _threads > 1 else _load().ora_insert_pnn_rows
+    sk = fn(_ptr(sum_), _ptr(cnt), nx, ny, nz, _ptr(images), n, H, W, _ptr(poses),
+            _ptr(_f64(calib, 16)), float(sx), float(sy), _ptr(_f64(spacing, 3)),
+            _ptr(_f64(origin, 3)), _ptr(fr) if fr is not None else None)
     return sum_, cnt, int(sk)
 
 

@@ -93,6 +93,10 @@ def analytic_grad(w, poses, band, eps, target):
         fr = q - i0
         i0 = i0.astype(np.int64)
         I = w.images[f].reshape(-1).astype(np.float64)
+        # float32 samples that are not finite or exceed 2^64 are not inserted
+        # (the C oracle's sample rule), so they carry no gradient
+        admit = np.abs(I) <= 2.0 ** 64
+        I = np.where(admit, I, 0.0)
         dq = np.zeros_like(q)
         for c in range(8):
             cc = np.array([c & 1, (c >> 1) & 1, c >> 2])
@@ -100,7 +104,7 @@ def analytic_grad(w, poses, band, eps, target):
             phi = np.where(cc[None, :] == 1, fr, 1.0 - fr)
             wgt = phi.prod(axis=1)
             ok = ((X[:, 0] >= 0) & (X[:, 0] < nx) & (X[:, 1] >= 0) & (X[:, 1] < ny) &
-                  (X[:, 2] >= lo) & (X[:, 2] < hi) & (wgt >= WMIN))
+                  (X[:, 2] >= lo) & (X[:, 2] < hi) & (wgt >= WMIN) & admit)
             if not ok.any():
                 continue
             Xo = X[ok]

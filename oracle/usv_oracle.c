@@ -41,8 +41,28 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define TWO32 4294967296.0
+
+/* Host threads for the multi-core forms (ora_insert_pnn_rows_mt, and the
+ * fill and projection loops, which split their independent outputs).  1
+ * (the default) runs everything on the calling thread, exactly the plain
+ * loops below.  Without OpenMP the count stays 1. */
+static int g_threads = 1;
+
+int ora_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
 
 /* Round half away from zero, exactly.  x - trunc(x) is exact in binary
  * floating point, so the comparison with 0.5 decides the tie rule. */
@@ -173,6 +193,48 @@ int64_t ora_insert_pnn_rows(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz
     return skipped;
 }
 
+/* ora_insert_pnn_rows on g_threads host threads: the frames are split into
+ * contiguous ranges and every accumulator update is an atomic integer add,
+ * so the result is the same bits as the plain loop whatever the order. */
+int64_t ora_insert_pnn_rows_mt(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz,
+                               const uint8_t *images, int n, int H, int W, const double *poses,
+                               const double K[16], double sx, double sy,
+                               const double spacing[3], const double origin[3],
+                               const int32_t *first_rows)
+{
+    int64_t skipped = 0;
+    const int64_t half = (int64_t)1 << 31;
+    const int64_t one = (int64_t)1 << 32;
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(+ : skipped)
+    for (int f = 0; f < n; ++f) {
+        int64_t c[9];
+        if (!ora_frame_affine_q32(poses + (size_t)f * 16, K, sx, sy, spacing, origin, c)) {
+            ++skipped;
+            continue;
+        }
+        const uint8_t *img = images + (size_t)f * H * W;
+        const int v_first = first_rows ? (first_rows[f] > 0 ? first_rows[f] : 0) : 0;
+        for (int v = v_first; v < H; ++v)
+            for (int u = 0; u < W; ++u) {
+                int64_t idx[3];
+                for (int a = 0; a < 3; ++a) {
+                    int64_t Q = c[6 + a] + (int64_t)u * c[a] + (int64_t)v * c[3 + a];
+                    idx[a] = floor_div(Q + half, one);
+                }
+                if (idx[0] < 0 || idx[0] >= nx || idx[1] < 0 || idx[1] >= ny || idx[2] < 0 ||
+                    idx[2] >= nz)
+                    continue;
+                size_t lin = ((size_t)idx[2] * ny + (size_t)idx[1]) * nx + (size_t)idx[0];
+                const uint64_t I = img[(size_t)v * W + u];
+#pragma omp atomic
+                sum[lin] += I;
+#pragma omp atomic
+                cnt[lin] += 1;
+            }
+    }
+    return skipped;
+}
+
 /* round-half-up mean of integer data: floor(s/c + 1/2) = (2s + c) / (2c) */
 static uint8_t mean_u8(uint64_t s, uint64_t c)
 {
@@ -192,6 +254,7 @@ static uint8_t mean_u8(uint64_t s, uint64_t c)
 void ora_fill_pnn(const uint64_t *sum, const uint32_t *cnt, int nx, int ny, int nz,
                   uint8_t *val, uint8_t *has)
 {
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y)
             for (int x = 0; x < nx; ++x) {
@@ -236,6 +299,7 @@ void ora_project_u8(const uint8_t *val, const uint8_t *has, int nx, int ny, int 
                     int hi, float *out, uint16_t *cnt)
 {
     (void)nz;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
             uint64_t s = 0, c = 0;
@@ -291,7 +355,10 @@ static void sample_point(const ora_geometry *g, int W, int i, int j, double *xi,
  * and, per axis, the map's values must be finite with |C_a| < 2^29 and the
  * per-step (linear: per pixel, A_a = M[a][0]*sx/s_a, B_a = M[a][2]*sy/s_a)
  * or per-mm (convex: M[a][0]/s_a, M[a][2]/s_a) factors below 2^14.
- * images: uint8 (is_f32 == 0) or float32, [n][H][W].
+ * images: uint8 (is_f32 == 0) or float32, [n][H][W].  Reading for float32
+ * samples (the paper's images are 8-bit, so it says nothing about them): a
+ * sample is inserted only if it is finite with |I| <= 2^64; any other is
+ * treated as absent and adds no weight.
  */
 int64_t ora_insert_trilinear(double *S, double *Wt, int nx, int ny, int nz,
                              const void *images, int is_f32, int n, int H, int W,
@@ -344,6 +411,8 @@ int64_t ora_insert_trilinear_rows(double *S, double *Wt, int nx, int ny, int nz,
                 }
                 double I = is_f32 ? (double)((const float *)images)[((size_t)f * H + i) * W + j]
                                   : (double)((const uint8_t *)images)[((size_t)f * H + i) * W + j];
+                if (!(fabs(I) <= 18446744073709551616.0)) /* not finite, or above 2^64 */
+                    continue;
                 for (int cz = 0; cz < 2; ++cz)
                     for (int cy = 0; cy < 2; ++cy)
                         for (int cx = 0; cx < 2; ++cx) {

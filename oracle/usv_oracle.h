@@ -16,6 +16,7 @@ typedef struct {
     double sector_deg; /* convex: full sector angle */
 } ora_geometry;
 
+int ora_set_threads(int n);
 int64_t ora_round_half_away(double x);
 int ora_frame_affine_q32(const double P[16], const double K[16], double sx, double sy,
                          const double spacing[3], const double origin[3], int64_t coef[9]);
@@ -38,6 +39,11 @@ int64_t ora_insert_pnn_rows(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz
                             const double K[16], double sx, double sy,
                             const double spacing[3], const double origin[3],
                             const int32_t *first_rows);
+int64_t ora_insert_pnn_rows_mt(uint64_t *sum, uint32_t *cnt, int nx, int ny, int nz,
+                               const uint8_t *images, int n, int H, int W, const double *poses,
+                               const double K[16], double sx, double sy,
+                               const double spacing[3], const double origin[3],
+                               const int32_t *first_rows);
 int64_t ora_insert_trilinear_rows(double *S, double *Wt, int nx, int ny, int nz,
                                   const void *images, int is_f32, int n, int H, int W,
                                   const double *poses, const double K[16],

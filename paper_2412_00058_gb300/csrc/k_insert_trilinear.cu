@@ -26,14 +26,18 @@
 // When the beam steps into a face-adjacent cell, the 4 corner voxels the two
 // cells share keep their terms in registers (moved to the new cell's
 // corners), and only the 4 corners left behind are sent: about 40 % fewer
-// atomics on the convex sweep.  This carry costs selects on every cell
+// atomics on the convex sweep.  This carry costs work on every cell
 // change; it pays where the atomics miss L2, and a launch can leave it out
 // (the pose-gradient path, whose smaller volume keeps its atomics in L2).
 // A conservative voxel box of the tile (FP64 extremes of the patch -- for a
 // convex fan the depth extreme can sit on the central beam -- plus a
 // one-voxel margin) decides whether the tile touches the grid at all and
-// whether its corners need bounds checks; a shared-memory box variant of
-// the accumulation is kept behind kUseBox.
+// whether its corners need bounds checks.
+//
+// Samples: a uint8 sample is always inserted; a float32 sample only if it is
+// finite with |I| <= 2^64 (one compare at load; a rejected sample adds no
+// weight).  This keeps every register sum of a column walk finite, so the
+// 0/1-mask carry below never multiplies an infinity by zero.
 #include <cfloat>
 #include <climits>
 
@@ -46,12 +50,6 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kCols = 256;                   // columns per tile (one per thread)
 constexpr int kMaxFpc = 8;                   // frames per CTA, at most
-constexpr int kBoxBytes = 64 * 1024;
-// Shared FP32 atomic adds measured as a read-retry loop on this part (430
-// instructions per sample, 32 % issue), so the shared box is kept only as
-// an option; tiles send merged cell terms straight to HBM vector atomics.
-constexpr bool kUseBox = false;
-constexpr int kBoxCap = kBoxBytes / 8;       // entries: one S and one W float each
 
 struct TriArgs {
     const void *img;
@@ -71,6 +69,7 @@ struct TriArgs {
 constexpr long long kOne47 = 1LL << 47;
 constexpr long long kMask47 = kOne47 - 1;
 constexpr float kWmin = 9.5367431640625e-07f;     // 2^-20
+constexpr float kMaxSample = 18446744073709551616.0f;  // 2^64: larger |I| is not inserted
 
 // q (FP64, |q| < 2^30) -> integer voxel floor(q) and Q16.47 fraction
 __device__ __forceinline__ void anchor(double q, int &i0, long long &fq)
@@ -138,8 +137,6 @@ __device__ void patch_box(const TriArgs &a, const FrameRec *r, int j0, int j1, i
     }
 }
 
-// Add one sample's 8 corner terms. Box mode: shared arrays, box-local key;
-// direct mode: HBM vector atomics.
 // Corners of a cell that a step to a face-adjacent cell leaves behind: the
 // step moves by one along the axis of corner bit `abit`, up or down; moving
 // up, the corners with that bit clear stay behind (the others become the
@@ -150,10 +147,10 @@ __device__ __forceinline__ bool left_behind(int c, bool face, int abit, bool up)
     return !face || (((c & abit) == 0) == up);
 }
 
-template <bool BOX, bool CHECK>
-__device__ __forceinline__ void splat(float *bS, float *bW, float2 *acc, unsigned ex,
-                                      unsigned ey, unsigned ez, int lx, int ly, int lz,
-                                      const float (&cS)[8], const float (&cW)[8],
+// Send a cell's corner terms to HBM, one vector atomic (S, W) per corner.
+template <bool CHECK>
+__device__ __forceinline__ void splat(float2 *acc, unsigned ex, unsigned ey, unsigned ez, int lx,
+                                      int ly, int lz, const float (&cS)[8], const float (&cW)[8],
                                       bool face = false, int abit = 1, bool up = true)
 {
 #pragma unroll
@@ -164,20 +161,14 @@ __device__ __forceinline__ void splat(float *bS, float *bW, float2 *acc, unsigne
         const unsigned X = (unsigned)(lx + cx), Y = (unsigned)(ly + cy), Z = (unsigned)(lz + cz);
         if (CHECK && !(X < ex && Y < ey && Z < ez))
             continue;
-        if (BOX) {
-            const unsigned k = X + ex * (Y + ey * Z);
-            atomicAdd(bS + k, cS[c]);
-            atomicAdd(bW + k, cW[c]);
-        } else {
-            atomicAdd(acc + ((size_t)Z * ey + Y) * ex + X, make_float2(cS[c], cW[c]));
-        }
+        atomicAdd(acc + ((size_t)Z * ey + Y) * ex + X, make_float2(cS[c], cW[c]));
     }
 }
 
-template <bool BOX, bool CHECK, bool CARRY>
+template <bool CHECK, bool CARRY>
 __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int f0, int f1,
-                                     int j, int v0, int v1, const int (&blo)[3], unsigned ex,
-                                     unsigned ey, unsigned ez, float *bS, float *bW)
+                                     int j, int v0, int v1, unsigned ex, unsigned ey,
+                                     unsigned ez)
 {
     for (int f = f0; f < f1; ++f) {
         const FrameRec *r = recs + (f - f0);
@@ -217,11 +208,14 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
             const float I = In;
             if (v + 1 < v1)
                 In = sample(v + 1);
+            // a float32 sample that is not finite or exceeds 2^64 is not
+            // inserted (uint8 samples always pass)
+            const bool admit = fabsf(I) <= kMaxSample;
             int ix[3];
             float w1[3], w0[3];
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
-                ix[ax] = i0[ax] + (int)(fq[ax] >> 47) - blo[ax];  // box-local (or global)
+                ix[ax] = i0[ax] + (int)(fq[ax] >> 47);
                 const long long fr = fq[ax] & kMask47;
                 tri_factors(fr, w1[ax], w0[ax]);
             }
@@ -237,8 +231,7 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
                 const int abit = dx != 0 ? 1 : dy != 0 ? 2 : 4;
                 const bool up = dx + dy + dz > 0;
                 if (cx0 != INT_MIN)
-                    splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW, face,
-                                      abit, up);
+                    splat<CHECK>(a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW, face, abit, up);
                 // new corner c is old corner c ^ abit when it receives: 0/1
                 // masks and multiply-adds (exact: one term is kept, the others
                 // are multiplied by zero) keep this off the integer pipe
@@ -278,7 +271,7 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
             for (int c = 0; c < 8; ++c) {
                 const float w = ((c & 1) ? w1[0] : w0[0]) * (((c >> 1) & 1) ? w1[1] : w0[1]) *
                                 ((c >> 2) ? w1[2] : w0[2]);
-                if (w >= kWmin) {
+                if (admit && w >= kWmin) {
                     cS[c] += w * I;
                     cW[c] += w;
                 }
@@ -290,16 +283,15 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
             }
         }
         if (cx0 != INT_MIN)
-            splat<BOX, CHECK>(bS, bW, a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW);
+            splat<CHECK>(a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW);
     }
 }
 
 template <bool CARRY>
 __global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
 {
-    extern __shared__ float tbox[];  // [kBoxCap] S, then [kBoxCap] W
     __shared__ FrameRec s_rec[kMaxFpc];
-    __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
+    __shared__ int s_mode, s_check;
     const int tx = blockIdx.x % a.tiles_x, ty = blockIdx.x / a.tiles_x;
     const int j0 = tx * kCols, j1 = min(a.W, j0 + kCols);
     const int v0 = ty * a.rows, v1 = min(a.H, v0 + a.rows);
@@ -329,7 +321,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
             int mode = 0, check = 0;
             if (any) {
                 const int n[3] = {a.nx, a.ny, a.nz};
-                long long vol = 1;
                 mode = 1;
                 for (int ax = 0; ax < 3; ++ax) {
                     // corners reach floor(q) + 1; one voxel of margin each side
@@ -340,62 +331,24 @@ __global__ void __launch_bounds__(kThreads, 3) k_insert_trilinear(TriArgs a)
                         mode = 0;
                     if (l != l0 || h != h0)
                         check = 1;
-                    s_lo[ax] = (int)l;
-                    s_ext[ax] = (int)(h >= l ? h - l + 1 : 0);
-                    vol *= (h >= l ? h - l + 1 : 0);
                 }
-                if (mode == 1 && (vol > kBoxCap || !kUseBox))
-                    mode = 2;
             }
             s_mode = mode;
             s_check = check;
         }
     }
     __syncthreads();
-    const int mode = s_mode;
-    if (mode == 0)
+    if (s_mode == 0)
         return;
     const int j = j0 + threadIdx.x;
-    const int rv0 = v0, rv1 = v1;
-    float *bS = tbox, *bW = tbox + kBoxCap;
-    if (mode == 2) {
-        // corner bounds checks only in tiles whose voxel box the grid clips
-        const int zero[3] = {0, 0, 0};
-        if (j < j1 && rv0 < rv1) {
-            if (s_check)
-                walk<false, true, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
-                                  (unsigned)a.ny, (unsigned)a.nz, bS, bW);
-            else
-                walk<false, false, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, zero, (unsigned)a.nx,
-                                   (unsigned)a.ny, (unsigned)a.nz, bS, bW);
-        }
-        return;
-    }
-    const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
-    const unsigned bvol = ex * ey * ez;
-    for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
-        bS[i] = 0.0f;
-        bW[i] = 0.0f;
-    }
-    __syncthreads();
-    const int blo[3] = {s_lo[0], s_lo[1], s_lo[2]};
-    if (j < j1 && rv0 < rv1) {
+    // corner bounds checks only in tiles whose voxel box the grid clips
+    if (j < j1 && v0 < v1) {
         if (s_check)
-            walk<true, true, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
+            walk<true, CARRY>(a, s_rec, f0, f1, j, v0, v1, (unsigned)a.nx, (unsigned)a.ny,
+                              (unsigned)a.nz);
         else
-            walk<true, false, CARRY>(a, s_rec, f0, f1, j, rv0, rv1, blo, ex, ey, ez, bS, bW);
-    }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (unsigned row = warp; row < ey * ez; row += kThreads / 32) {
-        const unsigned ly = row % ey, lz = row / ey;
-        float2 *dst = a.acc + ((size_t)(lz + s_lo[2]) * a.ny + (ly + s_lo[1])) * a.nx + s_lo[0];
-        const size_t o = (size_t)row * ex;
-        for (unsigned lx = lane; lx < ex; lx += 32) {
-            const float w = bW[o + lx];
-            if (w != 0.0f)
-                atomicAdd(dst + lx, make_float2(bS[o + lx], w));
-        }
+            walk<false, CARRY>(a, s_rec, f0, f1, j, v0, v1, (unsigned)a.nx, (unsigned)a.ny,
+                               (unsigned)a.nz);
     }
 }
 
@@ -456,20 +409,11 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535)
         return cudaErrorInvalidConfiguration;
-    if (kUseBox) {
-        cudaError_t e =
-            prepare_kernel(reinterpret_cast<const void *>(k_insert_trilinear<true>), kBoxBytes);
-        if (e == cudaSuccess)
-            e = prepare_kernel(reinterpret_cast<const void *>(k_insert_trilinear<false>),
-                               kBoxBytes);
-        if (e != cudaSuccess)
-            return e;
-    }
     dim3 grid(a.tiles_x * tiles_y, (unsigned)groups);
     if (carry)
-        k_insert_trilinear<true><<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);
+        k_insert_trilinear<true><<<grid, kThreads, 0, st>>>(a);
     else
-        k_insert_trilinear<false><<<grid, kThreads, kUseBox ? kBoxBytes : 0, st>>>(a);
+        k_insert_trilinear<false><<<grid, kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 

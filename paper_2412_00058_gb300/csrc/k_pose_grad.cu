@@ -17,8 +17,9 @@
 //     w >= 2^-20); dL/dp_s = dL/dq_s / spacing
 //   per frame, for the left perturbation p' = R(w) (p - c) + c + t about the
 //   frame centre c: dL/dt = sum_s dL/dp_s,  dL/dw = sum_s (p_s - c) x dL/dp_s.
-// Samples reuse the insertion kernel's exact fixed-point positions, so
-// forward and backward see identical cells.
+// Samples reuse the insertion kernel's exact fixed-point positions and its
+// sample rule (float32 samples that are not finite or exceed 2^64 are not
+// inserted), so forward and backward see identical cells.
 #include <cfloat>
 
 #include "usv_internal.cuh"
@@ -30,6 +31,7 @@ namespace {
 constexpr long long kOne47 = 1LL << 47;
 constexpr long long kMask47 = kOne47 - 1;
 constexpr float kWmin = 9.5367431640625e-07f;     // 2^-20
+constexpr float kMaxSample = 18446744073709551616.0f;  // 2^64, as the insertion
 
 __device__ __forceinline__ void anchor(double q, int &i0, long long &fq)
 {
@@ -136,6 +138,9 @@ __global__ void __launch_bounds__(256) k_pose_grad(GradArgs a, int tiles_x)
                 const size_t pi = ((size_t)f * a.H + v) * a.W + j;
                 const float I = a.is_f32 ? __ldg(static_cast<const float *>(a.img) + pi)
                                          : u8_to_float(__ldg(static_cast<const uint8_t *>(a.img) + pi));
+                // the insertion's sample rule: a float32 sample that is not
+                // finite or exceeds 2^64 was not inserted, so it has no gradient
+                const bool admit = fabsf(I) <= kMaxSample;
                 int ix[3];
                 float w1[3], w0[3], rel[3];
 #pragma unroll
@@ -157,7 +162,7 @@ __global__ void __launch_bounds__(256) k_pose_grad(GradArgs a, int tiles_x)
                         continue;
                     const float px = cx ? w1[0] : w0[0], py = cy ? w1[1] : w0[1],
                                 pz = cz ? w1[2] : w0[2];
-                    if (px * py * pz < kWmin)
+                    if (!admit || px * py * pz < kWmin)
                         continue;
                     const float2 ad = __ldg(a.adj + (size_t)(Z - a.lo) * plane +
                                             (size_t)Y * a.nx + X);

@@ -70,6 +70,76 @@ int cuda_rc(cudaError_t e)
 
 }  // namespace
 
+// Pinned host memory through which host-side poses reach the device: each
+// insertion launch copies its frames' poses (128 B per frame) into the ring,
+// then one asynchronous host->device copy on the caller's stream takes them
+// to the volume's device pose slot.  A region of the ring is written again
+// only after the copy that read it has completed (an event per region), so
+// the host can run several calls ahead of the device.
+class PoseRing {
+public:
+    static constexpr size_t kBytes = 2u << 20;  // 2 MB: four full launches of 4096 frames
+    static constexpr int kMaxInFlight = 64;
+
+    cudaError_t init()
+    {
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&base_), kBytes,
+                                      cudaHostAllocDefault);
+        for (int i = 0; e == cudaSuccess && i < kMaxInFlight; ++i)
+            e = cudaEventCreateWithFlags(&ev_[i], cudaEventDisableTiming);
+        return e;
+    }
+    ~PoseRing()
+    {
+        for (int i = 0; i < kMaxInFlight; ++i)
+            if (ev_[i])
+                cudaEventDestroy(ev_[i]);
+        if (base_)
+            cudaFreeHost(base_);
+    }
+
+    // Stage `bytes` (<= kBytes) from `src` and copy them to `dst_dev` on `st`.
+    cudaError_t stage(const void *src, size_t bytes, void *dst_dev, cudaStream_t st)
+    {
+        size_t off = head_;
+        if (off + bytes > kBytes)
+            off = 0;  // wrap: regions never straddle the end
+        // wait for the oldest in-flight regions until [off, off + bytes) is free
+        while (count_ > 0 && (overlaps(first_, off, bytes) || count_ == kMaxInFlight)) {
+            cudaError_t e = cudaEventSynchronize(ev_[first_]);
+            if (e != cudaSuccess)
+                return e;
+            first_ = (first_ + 1) % kMaxInFlight;
+            --count_;
+        }
+        std::memcpy(base_ + off, src, bytes);
+        cudaError_t e = cudaMemcpyAsync(dst_dev, base_ + off, bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess)
+            return e;
+        const int slot = (first_ + count_) % kMaxInFlight;
+        e = cudaEventRecord(ev_[slot], st);
+        if (e != cudaSuccess)
+            return e;
+        use_off_[slot] = off;
+        use_bytes_[slot] = bytes;
+        ++count_;
+        head_ = off + bytes;
+        return cudaSuccess;
+    }
+
+private:
+    bool overlaps(int slot, size_t off, size_t bytes) const
+    {
+        return use_off_[slot] < off + bytes && off < use_off_[slot] + use_bytes_[slot];
+    }
+
+    char *base_ = nullptr;
+    size_t head_ = 0;
+    cudaEvent_t ev_[kMaxInFlight] = {};
+    size_t use_off_[kMaxInFlight] = {}, use_bytes_[kMaxInFlight] = {};
+    int first_ = 0, count_ = 0;
+};
+
 Layout layout_for(usv_grid g, int mode)
 {
     Layout L{};
@@ -86,6 +156,8 @@ Layout layout_for(usv_grid g, int mode)
     off += align_up((size_t)kRecCap * sizeof(FrameRec));
     L.beams = off;
     off += align_up((size_t)kBeamCap * sizeof(double2));
+    L.poses = off;
+    off += align_up((size_t)kRecCap * 16 * sizeof(double));
     L.status = off;
     off += kAlign;
     L.spare = 0;
@@ -177,6 +249,20 @@ int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double or
     v->status = reinterpret_cast<uint32_t *>(v->base + L.status);
     v->num_sms = sms;
     v->device = attr.device;
+    v->pose_slot = reinterpret_cast<double *>(v->base + L.poses);
+    v->ring = new (std::nothrow) usv::PoseRing();
+    if (!v->ring) {
+        delete v;
+        return USV_ERR_NOMEM;
+    }
+    {
+        usv::DeviceGuard g(attr.device);
+        if (int rc = usv::cuda_rc(v->ring->init())) {
+            delete v->ring;
+            delete v;
+            return rc;
+        }
+    }
     *out = reinterpret_cast<usv_volume *>(v);
     return USV_OK;
 }
@@ -185,7 +271,12 @@ int usv_volume_destroy(usv_volume *vol)
 {
     if (!vol)
         return USV_ERR_ARG;
-    delete reinterpret_cast<Volume *>(vol);
+    Volume *v = reinterpret_cast<Volume *>(vol);
+    {
+        usv::DeviceGuard g(v->device);
+        delete v->ring;  // waits for nothing: the caller's stream owns the pending copies
+    }
+    delete v;
     return USV_OK;
 }
 
@@ -206,18 +297,106 @@ int usv_volume_reset(usv_volume *vol, void *stream)
 namespace usv {
 // acc_override / cfg_override: insert into other accumulators with a given
 // tile shape (the autotuner); null = the volume's own, tile_for().
+// poses_on_host: `poses` is host memory, staged through the volume's pinned
+// ring into its device pose slot launch by launch.
 int insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
-                int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                int32_t dtype, const double *poses, const usv_calibration *cal,
                 const int32_t *first_rows_dev, void *stream, void *acc_override = nullptr,
                 const TileCfg *cfg_override = nullptr, int tri_min_rows = 8,
-                bool tri_carry = true);
+                bool tri_carry = true, bool poses_on_host = false);
 }
 
 int usv_insert_frames(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
-                      int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                      int32_t dtype, const double *poses_host, const usv_calibration *cal,
                       void *stream)
 {
+    return usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_host, cal, nullptr, stream,
+                            nullptr, nullptr, 8, true, true);
+}
+
+int usv_insert_frames_dev(usv_volume *vol, const void *images_dev, int32_t n, int32_t H,
+                          int32_t W, int32_t dtype, const double *poses_dev,
+                          const usv_calibration *cal, void *stream)
+{
     return usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream);
+}
+
+int usv_frames_voxel_box(usv_grid grid, const double spacing_mm[3], const double origin_mm[3],
+                         const double *poses_host, int32_t n, int32_t H, int32_t W,
+                         const usv_calibration *cal, int32_t margin, int32_t lo[3], int32_t hi[3])
+{
+    if (!cal || !lo || !hi || n < 0 || H < 1 || W < 1 || margin < 0)
+        return USV_ERR_ARG;
+    if (!usv::grid_ok(grid) || !usv::finite3(spacing_mm) || !usv::finite3(origin_mm) ||
+        !(spacing_mm[0] > 0.0 && spacing_mm[1] > 0.0 && spacing_mm[2] > 0.0))
+        return USV_ERR_ARG;
+    if (n > 0 && !poses_host)
+        return USV_ERR_ARG;
+    if (!usv::affine_ok(cal->image_to_probe))
+        return USV_ERR_ARG;
+    // the frame's in-plane extent (x, z in mm of the image frame): a
+    // rectangle for a linear probe; for a convex one the sector's bounding
+    // rectangle (x = r sin theta, z = r cos theta - r0)
+    double x0, x1, z0, z1;
+    if (cal->geom == USV_CONVEX) {
+        if (!(std::isfinite(cal->r0_mm) && std::isfinite(cal->dr_mm) &&
+              std::isfinite(cal->sector_deg) && cal->r0_mm >= 0.0 && cal->dr_mm > 0.0 &&
+              cal->sector_deg > 0.0 && cal->sector_deg < 180.0))
+            return USV_ERR_ARG;
+        const double half = cal->sector_deg * 3.14159265358979323846 / 360.0;
+        const double R = cal->r0_mm + (double)(H - 1) * cal->dr_mm;
+        x0 = -R * std::sin(half);
+        x1 = R * std::sin(half);
+        z0 = cal->r0_mm * std::cos(half) - cal->r0_mm;
+        z1 = R - cal->r0_mm;
+    } else if (cal->geom == USV_LINEAR) {
+        if (!(std::isfinite(cal->sx_mm) && std::isfinite(cal->sy_mm) && cal->sx_mm > 0.0 &&
+              cal->sy_mm > 0.0))
+            return USV_ERR_ARG;
+        x0 = 0.0;
+        x1 = (double)(W - 1) * cal->sx_mm;
+        z0 = 0.0;
+        z1 = (double)(H - 1) * cal->sy_mm;
+    } else {
+        return USV_ERR_ARG;
+    }
+    const double *K = cal->image_to_probe;
+    double qlo[3] = {INFINITY, INFINITY, INFINITY}, qhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int f = 0; f < n; ++f) {
+        const double *P = poses_host + (size_t)f * 16;
+        if (!usv::affine_ok(P))
+            continue;  // skipped by the insertion too
+        for (int c = 0; c < 4; ++c) {
+            const double pt[4] = {(c & 1) ? x1 : x0, 0.0, (c & 2) ? z1 : z0, 1.0};
+            double kp[4];
+            for (int i = 0; i < 4; ++i)
+                kp[i] = K[4 * i] * pt[0] + K[4 * i + 1] * pt[1] + K[4 * i + 2] * pt[2] +
+                        K[4 * i + 3] * pt[3];
+            for (int a = 0; a < 3; ++a) {
+                const double w = P[4 * a] * kp[0] + P[4 * a + 1] * kp[1] + P[4 * a + 2] * kp[2] +
+                                 P[4 * a + 3] * kp[3];
+                const double q = (w - origin_mm[a]) / spacing_mm[a];
+                qlo[a] = std::min(qlo[a], q);
+                qhi[a] = std::max(qhi[a], q);
+            }
+        }
+    }
+    const int gn[3] = {grid.nx, grid.ny, grid.nz};
+    for (int a = 0; a < 3; ++a) {
+        if (!(qlo[a] <= qhi[a]) || !std::isfinite(qlo[a]) || !std::isfinite(qhi[a])) {
+            lo[0] = lo[1] = lo[2] = hi[0] = hi[1] = hi[2] = 0;  // no valid frame: empty
+            return USV_OK;
+        }
+    }
+    for (int a = 0; a < 3; ++a) {
+        // voxels written: nearest (floor(q + 1/2)) or trilinear corners
+        // (floor(q), floor(q) + 1); one more voxel each side absorbs the
+        // rounding of this FP64 evaluation against the exact insertion map
+        const double l = std::floor(qlo[a]) - 1.0 - margin, h = std::floor(qhi[a]) + 3.0 + margin;
+        lo[a] = (int32_t)std::max(0.0, std::min((double)gn[a], l));
+        hi[a] = (int32_t)std::max(0.0, std::min((double)gn[a], h));
+    }
+    return USV_OK;
 }
 
 int usv_insert_frames_cut(usv_volume *vol, const void *images_dev, int32_t n, int32_t H,
@@ -351,15 +530,18 @@ int usv_apply_pose_delta(const double *poses_dev, const double *delta_dev, int32
 }
 
 int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
-                     int32_t dtype, const double *poses_dev, const usv_calibration *cal,
+                     int32_t dtype, const double *poses, const usv_calibration *cal,
                      const int32_t *first_rows_dev, void *stream, void *acc_override,
-                     const TileCfg *cfg_override, int tri_min_rows, bool tri_carry)
+                     const TileCfg *cfg_override, int tri_min_rows, bool tri_carry,
+                     bool poses_on_host)
 {
     if (!vol || !cal || n < 0)
         return USV_ERR_ARG;
     if (n == 0)
         return USV_OK;
-    if (!images_dev || !poses_dev || (reinterpret_cast<uintptr_t>(poses_dev) & 7) != 0)
+    if (!images_dev || !poses)
+        return USV_ERR_ARG;
+    if (!poses_on_host && (reinterpret_cast<uintptr_t>(poses) & 7) != 0)
         return USV_ERR_ARG;
     if (H < 1 || W < 1)
         return USV_ERR_ARG;
@@ -407,6 +589,15 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
 
     usv::DeviceGuard g(v.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (poses_on_host) {
+        // the staging ring's host-side waits and copies from host memory
+        // have no place in a captured graph: capture the device-pose form
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (int rc = usv::cuda_rc(cudaStreamIsCapturing(st, &cs)))
+            return rc;
+        if (cs != cudaStreamCaptureStatusNone)
+            return USV_ERR_UNSUPPORTED;
+    }
     const size_t elt = dtype == USV_U8 ? 1 : 4;
     const size_t frame_bytes = (size_t)H * W * elt;
     cudaError_t e = cudaSuccess;
@@ -415,7 +606,14 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
     for (int c0 = 0; c0 < n && e == cudaSuccess; c0 += usv::kRecCap) {
         const int nc = n - c0 < usv::kRecCap ? n - c0 : usv::kRecCap;
         sp.first_rows = first_rows_dev ? first_rows_dev + c0 : nullptr;
-        e = usv::launch_frame_setup(poses_dev + (size_t)c0 * 16, nc, sp, v.rec, v.status, st);
+        const double *pc = poses + (size_t)c0 * 16;
+        if (poses_on_host) {
+            e = v.ring->stage(pc, (size_t)nc * 16 * sizeof(double), v.pose_slot, st);
+            if (e != cudaSuccess)
+                break;
+            pc = v.pose_slot;
+        }
+        e = usv::launch_frame_setup(pc, nc, sp, v.rec, v.status, st);
         if (e != cudaSuccess)
             break;
         const char *img = static_cast<const char *>(images_dev) + (size_t)c0 * frame_bytes;
@@ -855,4 +1053,16 @@ int usv_test_fill_wait_timeout(usv_volume *vol, int32_t plane, void *stream)
     const cudaError_t e =
         usv::launch_fill_pnn(v, lo, hi, static_cast<cudaStream_t>(stream), nullptr, plane);
     return e == cudaErrorNotSupported ? USV_ERR_UNSUPPORTED : usv::cuda_rc(e);
+}
+
+int usv_test_insert_trilinear_carry(usv_volume *vol, const void *images_dev, int32_t n,
+                                    int32_t H, int32_t W, int32_t dtype, const double *poses_dev,
+                                    const usv_calibration *cal, int32_t carry, void *stream)
+{
+    if (!vol)
+        return USV_ERR_ARG;
+    if (reinterpret_cast<Volume *>(vol)->mode != USV_TRILINEAR)
+        return USV_ERR_UNSUPPORTED;
+    return usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream,
+                            nullptr, nullptr, 8, carry != 0);
 }

@@ -35,6 +35,8 @@ struct TunedTile {
     TileCfg cfg;
 };
 
+class PoseRing;  // pinned host staging of host-side poses (usv_api.cu)
+
 struct Volume {
     usv_grid g;
     double spacing[3];
@@ -54,6 +56,8 @@ struct Volume {
     int device;
     TunedTile tuned[kTunedCap];  // tile shapes set or tuned per frame size
     int ntuned;
+    double *pose_slot;  // device: poses of one insertion launch, copied from host poses
+    PoseRing *ring;     // host poses staged here before their copy (owned by the handle)
 };
 
 // The tile for frames of H x W in this volume: a tuned or set one, else the
@@ -67,7 +71,7 @@ constexpr int kBeamCap = 32768;    // max W
 constexpr int kMaxDim = 32768;     // max H, W
 
 struct Layout {
-    size_t acc, val, mask, rec, beams, status, spare, total;  // spare: 0 if none
+    size_t acc, val, mask, rec, beams, poses, status, spare, total;  // spare: 0 if none
 };
 Layout layout_for(usv_grid g, int mode);  // mode may carry USV_SPARE_ACCUM
 

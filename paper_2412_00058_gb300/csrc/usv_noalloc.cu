@@ -34,29 +34,82 @@ static __device__ __align__(256) FrameRec g_noalloc_rec[kNoAllocFrames];
 static __device__ __align__(256) uint32_t g_noalloc_status[64];
 
 constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-FrameRec *g_rec_ptr[kMaxDevices];
-uint32_t *g_status_ptr[kMaxDevices];
 
-// Device addresses of the scratch on the current device, looked up once per
-// device with that device current.  (In host code the symbols are only
-// host-side stand-ins; their device addresses must be asked for.)
-cudaError_t scratch_for(int dev, FrameRec **rec, uint32_t **status)
+// Per device: the scratch's device addresses and the SM count, looked up
+// with that device current, and the id of the CUDA context they belong to.
+// A context destroyed and created again (cudaDeviceReset) loads the library's
+// module anew, so the addresses are looked up again for the new context.
+struct DeviceScratch {
+    unsigned long long ctx_id;
+    FrameRec *rec;
+    uint32_t *status;
+    int num_sms;
+};
+std::mutex g_mu;
+DeviceScratch g_dev[kMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Id of the current context (driver entry points, fetched once); 0 if the
+// driver does not provide one, in which case the first lookup is kept (ids
+// are unique for the life of the process and never 0).
+unsigned long long current_ctx_id()
 {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+        cudaGetLastError();
+    });
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0)
+        return id;
+    return 0;
+}
+
+// The scratch of device `dev` (current) in its current context.  In host
+// code the symbols are only host-side stand-ins; their device addresses
+// must be asked for, once per device and context.
+cudaError_t scratch_for(int dev, DeviceScratch *out)
+{
+    // cudaSetDevice initialises the device's primary context and makes it
+    // current, so the context id below is that of the context the next
+    // launch uses (also right after a cudaDeviceReset)
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess)
+        return e;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_rec_ptr[dev]) {
+    DeviceScratch &d = g_dev[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!d.rec || id != d.ctx_id) {
         void *r = nullptr, *s = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&r, g_noalloc_rec);
+        int sms = 0;
+        e = cudaGetSymbolAddress(&r, g_noalloc_rec);
+        if (e == cudaSuccess)
+            e = cudaGetSymbolAddress(&s, g_noalloc_status);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess)
             return e;
-        e = cudaGetSymbolAddress(&s, g_noalloc_status);
-        if (e != cudaSuccess)
-            return e;
-        g_rec_ptr[dev] = static_cast<FrameRec *>(r);
-        g_status_ptr[dev] = static_cast<uint32_t *>(s);
+        d.rec = static_cast<FrameRec *>(r);
+        d.status = static_cast<uint32_t *>(s);
+        d.num_sms = sms;
+        d.ctx_id = id;
     }
-    *rec = g_rec_ptr[dev];
-    *status = g_status_ptr[dev];
+    *out = d;
     return cudaSuccess;
 }
 
@@ -107,9 +160,8 @@ extern "C" int usv_insert_pnn_noalloc(uint64_t *accum_dev, usv_grid grid,
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= usv::kMaxDevices)
         return USV_ERR_CUDA;
-    usv::FrameRec *rec = nullptr;
-    uint32_t *scratch_status = nullptr;
-    if (usv::scratch_for(dev, &rec, &scratch_status) != cudaSuccess)
+    usv::DeviceScratch sc;
+    if (usv::scratch_for(dev, &sc) != cudaSuccess)
         return USV_ERR_CUDA;
 
     // A stack-only view of the caller's accumulators for the shared launchers.
@@ -118,9 +170,10 @@ extern "C" int usv_insert_pnn_noalloc(uint64_t *accum_dev, usv_grid grid,
     v.g = grid;
     v.mode = USV_PNN;
     v.acc = accum_dev;
-    v.rec = rec;
-    v.status = status_dev ? status_dev : scratch_status;
+    v.rec = sc.rec;
+    v.status = status_dev ? status_dev : sc.status;
     v.device = dev;
+    v.num_sms = sc.num_sms;  // lets small batches spread over the GPU, as usv_insert_frames
     usv::SetupParams sp;
     std::memcpy(sp.K, cal->image_to_probe, sizeof(sp.K));
     for (int a = 0; a < 3; ++a) {

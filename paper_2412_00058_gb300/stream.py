@@ -30,7 +30,6 @@ schedules.
 """
 from __future__ import annotations
 
-import math
 import threading
 import time
 from dataclasses import dataclass, field
@@ -45,33 +44,6 @@ MAX_BURST = 32
 
 class AdmissionError(RuntimeError):
     """A session does not fit the device-memory budget."""
-
-
-def in_plane_extent(w):
-    """(x_min, x_max, z_min, z_max) of a frame in the image plane (mm)."""
-    if w.geom == "convex":
-        half = math.radians(w.sector_deg) / 2.0
-        R = w.r0 + (w.H - 1) * w.dr
-        return (-R * math.sin(half), R * math.sin(half), w.r0 * math.cos(half) - w.r0, R - w.r0)
-    return (0.0, (w.W - 1) * w.sx, 0.0, (w.H - 1) * w.sy)
-
-
-def frames_voxel_box(w, poses: np.ndarray, margin: int = 2):
-    """Half-open voxel box [lo, hi) holding every voxel the frames can write
-    (nearest voxel or trilinear corners) widened by `margin` voxels, clipped
-    to the grid.  Exact for the frame corners: the map is affine in the
-    image plane and the in-plane extent is a rectangle."""
-    x0, x1, z0, z1 = in_plane_extent(w)
-    pts = np.array([[x, 0.0, z, 1.0] for x in (x0, x1) for z in (z0, z1)]).T  # 4 x 4
-    M = np.einsum("fij,jk->fik", poses.reshape(-1, 4, 4), np.asarray(w.calib).reshape(4, 4))
-    q = (np.einsum("fij,jc->fic", M, pts)[:, :3, :] - np.asarray(w.origin)[None, :, None]) / \
-        np.asarray(w.spacing)[None, :, None]
-    qmin = q.min(axis=(0, 2))
-    qmax = q.max(axis=(0, 2))
-    n = np.asarray(w.grid)
-    lo = np.clip(np.floor(qmin).astype(np.int64) - margin, 0, n)
-    hi = np.clip(np.floor(qmax).astype(np.int64) + 2 + margin, 0, n)
-    return lo, hi
 
 
 def session_bytes(w) -> int:
@@ -134,15 +106,19 @@ class Session:
             yield t0 + (f + b) / self.fps, f, b
             f += b
 
-    def stage(self, f0: int, b: int, st):
-        """Host->device copy of burst [f0, f0 + b) into the staging buffers."""
+    def stage(self, f0: int, b: int, st, poses: bool = False):
+        """Host->device copy of burst [f0, f0 + b) into the staging buffers
+        (the frames; the poses too if `poses`, for the multi-volume call)."""
         self.d_imgs[:b].copy_(self.h_imgs[f0:f0 + b], non_blocking=True)
-        self.d_poses[:b].copy_(self.h_poses[f0:f0 + b], non_blocking=True)
+        if poses:
+            self.d_poses[:b].copy_(self.h_poses[f0:f0 + b], non_blocking=True)
 
     def refresh(self, f0: int, b: int, st):
-        """Fill + projection of the region burst [f0, f0 + b) touched."""
+        """Fill + projection of the region burst [f0, f0 + b) touched: the
+        library's voxel box of the burst, widened by the fill's one-voxel
+        neighbourhood."""
         w = self.w
-        lo, hi = frames_voxel_box(w, w.poses[f0:f0 + b])
+        lo, hi = self.vol.voxel_box(self.h_poses[f0:f0 + b], w.H, w.W, self.cal, margin=1)
         usvol.fill_holes_region(self.vol.handle, lo, hi, 1, st)
         usvol.project_depth_band_region(self.vol.handle, w.band[0], w.band[1], lo[:2], hi[:2],
                                         self.out.data_ptr(), self.cnt.data_ptr(), st)
@@ -152,7 +128,8 @@ class Session:
         st = self.stream
         with torch.cuda.stream(st):
             self.stage(f0, b, st)
-            self.vol.insert(self.d_imgs[:b], self.d_poses[:b], self.cal, st)
+            # host poses: the library stages them (usv_insert_frames)
+            self.vol.insert(self.d_imgs[:b], self.h_poses[f0:f0 + b], self.cal, st)
             self.refresh(f0, b, st)
             ev = torch.cuda.Event()
             ev.record(st)
@@ -197,7 +174,7 @@ class Scheduler:
         per session.  Returns the done-event."""
         with torch.cuda.stream(st):
             for si, f0, b in bursts:
-                self.sessions[si].stage(f0, b, st)
+                self.sessions[si].stage(f0, b, st, poses=self.sessions[si].w.mode == "pnn")
             pnn = [(si, b) for si, _, b in bursts if self.sessions[si].w.mode == "pnn"]
             if pnn:
                 usvol.insert_frames_multi(
@@ -206,7 +183,7 @@ class Scheduler:
             for si, f0, b in bursts:
                 s = self.sessions[si]
                 if s.w.mode != "pnn":
-                    s.vol.insert(s.d_imgs[:b], s.d_poses[:b], s.cal, st)
+                    s.vol.insert(s.d_imgs[:b], s.h_poses[f0:f0 + b], s.cal, st)
             for si, f0, b in bursts:
                 self.sessions[si].refresh(f0, b, st)
             ev = torch.cuda.Event()

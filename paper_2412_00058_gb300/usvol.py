@@ -38,7 +38,8 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_project_depth_band_region", "usv_insert_frames_cut", "usv_cut_rows_alg1",
            "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta",
            "usv_fill_holes_and_clear", "usv_tune_insert", "usv_set_tile_config",
-           "usv_get_tile_config", "usv_insert_frames_multi", "usv_test_fill_wait_timeout")
+           "usv_get_tile_config", "usv_insert_frames_multi", "usv_test_fill_wait_timeout",
+           "usv_insert_frames_dev", "usv_frames_voxel_box", "usv_test_insert_trilinear_carry")
 
 
 class UsvError(RuntimeError):
@@ -115,6 +116,16 @@ def lib():
             L.usv_volume_reset.restype = ctypes.c_int
             L.usv_insert_frames.argtypes = [P, P, I, I, I, I, P, ctypes.POINTER(Calibration), P]
             L.usv_insert_frames.restype = ctypes.c_int
+            L.usv_insert_frames_dev.argtypes = [P, P, I, I, I, I, P, ctypes.POINTER(Calibration),
+                                                 P]
+            L.usv_insert_frames_dev.restype = ctypes.c_int
+            I3o = ctypes.POINTER(ctypes.c_int32)
+            L.usv_frames_voxel_box.argtypes = [Grid, D3, D3, P, I, I, I,
+                                               ctypes.POINTER(Calibration), I, I3o, I3o]
+            L.usv_frames_voxel_box.restype = ctypes.c_int
+            L.usv_test_insert_trilinear_carry.argtypes = [P, P, I, I, I, I, P,
+                                                          ctypes.POINTER(Calibration), I, P]
+            L.usv_test_insert_trilinear_carry.restype = ctypes.c_int
             L.usv_fill_holes.argtypes = [P, I, P]
             L.usv_fill_holes.restype = ctypes.c_int
             L.usv_project_depth_band.argtypes = [P, I, I, P, P, P]
@@ -208,10 +219,43 @@ def volume_reset(handle: int, stream=None) -> None:
 
 
 def insert_frames(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
-                  poses_ptr: int, cal: Calibration, stream=None) -> None:
+                  poses_host_ptr: int, cal: Calibration, stream=None) -> None:
+    """Poses in host memory (staged by the library)."""
     _check(lib().usv_insert_frames(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H, W,
-                                   dtype, ctypes.c_void_p(poses_ptr), ctypes.byref(cal),
+                                   dtype, ctypes.c_void_p(poses_host_ptr), ctypes.byref(cal),
                                    ctypes.c_void_p(_stream_ptr(stream))), "usv_insert_frames")
+
+
+def insert_frames_dev(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
+                      poses_dev_ptr: int, cal: Calibration, stream=None) -> None:
+    """Poses in device memory."""
+    _check(lib().usv_insert_frames_dev(ctypes.c_void_p(handle), ctypes.c_void_p(images_ptr), n, H,
+                                       W, dtype, ctypes.c_void_p(poses_dev_ptr),
+                                       ctypes.byref(cal), ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_insert_frames_dev")
+
+
+def frames_voxel_box(grid, spacing, origin, poses_host_ptr: int, n: int, H: int, W: int,
+                     cal: Calibration, margin: int = 0):
+    """(lo, hi): the half-open voxel box the frames can write, widened by margin."""
+    lo = (ctypes.c_int32 * 3)()
+    hi = (ctypes.c_int32 * 3)()
+    _check(lib().usv_frames_voxel_box(Grid(*grid), _d3(spacing), _d3(origin),
+                                      ctypes.c_void_p(poses_host_ptr), n, H, W, ctypes.byref(cal),
+                                      int(margin), lo, hi), "usv_frames_voxel_box")
+    return tuple(lo), tuple(hi)
+
+
+def insert_trilinear_carry(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
+                           poses_dev_ptr: int, cal: Calibration, carry: bool,
+                           stream=None) -> None:
+    """Test hook: trilinear insertion with the corner carry on or off."""
+    _check(lib().usv_test_insert_trilinear_carry(ctypes.c_void_p(handle),
+                                                 ctypes.c_void_p(images_ptr), n, H, W, dtype,
+                                                 ctypes.c_void_p(poses_dev_ptr), ctypes.byref(cal),
+                                                 1 if carry else 0,
+                                                 ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_test_insert_trilinear_carry")
 
 
 def insert_frames_cut(handle: int, images_ptr: int, n: int, H: int, W: int, dtype: int,
@@ -405,14 +449,31 @@ class Volume:
     def reset(self, stream=None):
         volume_reset(self.handle, stream)
 
-    def insert(self, images: torch.Tensor, poses: torch.Tensor, cal: Calibration, stream=None):
-        assert images.is_cuda and poses.is_cuda and images.is_contiguous() and poses.is_contiguous()
-        assert poses.dtype == torch.float64
+    def insert(self, images: torch.Tensor, poses, cal: Calibration, stream=None):
+        """Insert frames (device tensor [n, H, W]); poses [n, 4, 4] float64 on
+        the device (usv_insert_frames_dev) or on the host -- a CPU tensor or
+        a numpy array -- (usv_insert_frames, staged by the library)."""
+        assert images.is_cuda and images.is_contiguous()
         n, H, W = images.shape
         dt = U8 if images.dtype == torch.uint8 else F32
         if dt == F32:
             assert images.dtype == torch.float32
-        insert_frames(self.handle, images.data_ptr(), n, H, W, dt, poses.data_ptr(), cal, stream)
+        if isinstance(poses, np.ndarray):
+            poses = torch.from_numpy(np.ascontiguousarray(poses, dtype=np.float64))
+        assert poses.dtype == torch.float64 and poses.is_contiguous()
+        if poses.is_cuda:
+            insert_frames_dev(self.handle, images.data_ptr(), n, H, W, dt, poses.data_ptr(), cal,
+                              stream)
+        else:
+            insert_frames(self.handle, images.data_ptr(), n, H, W, dt, poses.data_ptr(), cal,
+                          stream)
+
+    def voxel_box(self, poses, H: int, W: int, cal: Calibration, margin: int = 0):
+        """usv_frames_voxel_box for host poses [n, 4, 4] (numpy or CPU tensor)."""
+        p = np.ascontiguousarray(poses.numpy() if isinstance(poses, torch.Tensor) else poses,
+                                 dtype=np.float64)
+        return frames_voxel_box(self.grid, self.spacing, self.origin, p.ctypes.data, p.shape[0],
+                                H, W, cal, margin)
 
     def tune(self, images: torch.Tensor, poses: torch.Tensor, cal: Calibration, stream=None):
         """Autotune the insertion tile shape for these frames (scratch

@@ -76,22 +76,20 @@ int main(int argc, char **argv)
     const size_t bytes = usv_volume_bytes(grid, USV_PNN);
     if (bytes == 0)
         return 2;
-    void *storage = NULL, *d_images = NULL, *d_poses = NULL, *d_out = NULL, *d_cnt = NULL;
+    void *storage = NULL, *d_images = NULL, *d_out = NULL, *d_cnt = NULL;
     CHECK_CUDA(cudaMalloc(&storage, bytes));
     CHECK_CUDA(cudaMalloc(&d_images, frame_bytes));
-    CHECK_CUDA(cudaMalloc(&d_poses, pose_bytes));
     CHECK_CUDA(cudaMalloc(&d_out, plane * sizeof(float)));
     CHECK_CUDA(cudaMalloc(&d_cnt, plane * sizeof(uint16_t)));
     CHECK_CUDA(cudaMemcpy(d_images, images, frame_bytes, cudaMemcpyHostToDevice));
-    CHECK_CUDA(cudaMemcpy(d_poses, poses, pose_bytes, cudaMemcpyHostToDevice));
 
     cudaStream_t st;
     CHECK_CUDA(cudaStreamCreate(&st));
     usv_volume *vol = NULL;
     CHECK_USV(usv_volume_create(grid, spacing, origin, USV_PNN, storage, bytes, &vol));
     CHECK_USV(usv_volume_reset(vol, st));
-    CHECK_USV(usv_insert_frames(vol, d_images, n, H, W, USV_U8, (const double *)d_poses, &cal,
-                                st));
+    /* poses straight from host memory: the library stages them */
+    CHECK_USV(usv_insert_frames(vol, d_images, n, H, W, USV_U8, poses, &cal, st));
     CHECK_USV(usv_fill_holes(vol, 1, st));
     CHECK_USV(usv_project_depth_band(vol, z_lo, z_hi, (float *)d_out, (uint16_t *)d_cnt, st));
     const int status = usv_status(vol, st);  /* waits for the stream */
@@ -116,7 +114,6 @@ int main(int argc, char **argv)
     cudaStreamDestroy(st);
     cudaFree(storage);
     cudaFree(d_images);
-    cudaFree(d_poses);
     cudaFree(d_out);
     cudaFree(d_cnt);
     free(poses);

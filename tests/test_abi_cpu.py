@@ -30,7 +30,7 @@ def test_header_symbols_exported(usvol):
     L = usvol.lib()
     for n in names:
         assert hasattr(L, n), f"{n} not exported by libusvol.so"
-    assert L.usv_abi_version() == 1
+    assert L.usv_abi_version() == 2
 
 
 def test_library_is_sm103a_build(usvol):
@@ -77,6 +77,10 @@ def test_calls_on_null_handle_fail_cleanly(usvol):
     L = usvol.lib()
     cal = usvol.make_calibration([1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1], sx=0.3, sy=0.3)
     assert L.usv_insert_frames(None, None, 1, 4, 4, 0, None, ctypes.byref(cal), None) == usvol.ERR_ARG
+    assert L.usv_insert_frames_dev(None, None, 1, 4, 4, 0, None, ctypes.byref(cal),
+                                   None) == usvol.ERR_ARG
+    assert L.usv_test_insert_trilinear_carry(None, None, 1, 4, 4, 0, None, ctypes.byref(cal), 1,
+                                             None) == usvol.ERR_ARG
     assert L.usv_fill_holes(None, 1, None) == usvol.ERR_ARG
     assert L.usv_project_depth_band(None, 0, 1, None, None, None) == usvol.ERR_ARG
     assert L.usv_volume_read(None, 0, None, None) == usvol.ERR_ARG

@@ -1,6 +1,7 @@
 """bench.py prints one JSON line with the keys its consumers read: the CPU
-reference arm (the oracle on bounded samples) here, and a short GPU run on
-a 600-frame piece of the sweep on the GPU."""
+reference arm (the oracle on all host cores, the whole sweep every step;
+here a 600-frame piece of it) on the CPU, and a short GPU run on a 600-frame
+piece of the sweep on the GPU."""
 import json
 import os
 import subprocess
@@ -23,12 +24,14 @@ def run_bench(*args, timeout=600):
 
 
 def test_reference_arm_line():
-    d = run_bench("--impl", "reference", "--steps", "2", "--warmup", "1")
+    d = run_bench("--impl", "reference", "--steps", "2", "--warmup", "1", "--frames", "600")
     assert BASE_KEYS <= set(d)
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "frames/s"
     assert d["steps"] == 2 and d["warmup"] == 1 and d["higher_is_better"] is True
     cb = d["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"]
+    assert 1 <= cb["cores"] <= len(os.sched_getaffinity(0))
+    assert abs(d["ms_per_step"] - 600 / d["value"] * 1e3) < 1e-6 * d["ms_per_step"]
     assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
 
@@ -49,6 +52,9 @@ def test_gpu_arm_line():
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == 600 * 640 * 480 + 600 * 128
     assert e["d2h_bytes_per_step"] > 0
+    assert e["host_link"]["h2d_gbs"] > 0 and 0 < e["host_link"]["frac"] < 1.5
+    pr = d["pipeline_roofline"]
+    assert pr["clear_bytes_per_step"] > 0 and 0 < pr["frac"] < 2
     assert set(d["stage_ms"]) == {"insert", "fill", "project", "gaps"}
     assert d["cuda_graph"]["ms_per_step"] > 0 and d["autotune"]["tile"]
     clocks = d["clocks"]

@@ -1,7 +1,9 @@
 """The library used from plain C (tests/c/usvol_c_example.c): the program
 includes only usvol.h and the CUDA runtime, takes device memory from
-cudaMalloc, and its projection equals the CPU oracle's bit for bit.  The
-header alone is also compiled as C99 on the CPU."""
+cudaMalloc, passes the poses from host memory (the library stages them,
+usv_insert_frames as the C ABI defines it), and its projection equals the
+CPU oracle's bit for bit.  The header alone is also compiled as C99 on the
+CPU."""
 import os
 import subprocess
 
@@ -28,7 +30,7 @@ def _compile(out_path):
 
 def test_header_compiles_as_c99(tmp_path):
     src = tmp_path / "h.c"
-    src.write_text('#include "usvol.h"\nint main(void) { return usv_abi_version() == 1 ? 0 : 1; }\n')
+    src.write_text('#include "usvol.h"\nint main(void) { return usv_abi_version() == 2 ? 0 : 1; }\n')
     subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-c",
                     str(src), "-I", os.path.join(ROOT, "include"), "-o",
                     str(tmp_path / "h.o")], check=True, capture_output=True, text=True)

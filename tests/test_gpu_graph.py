@@ -1,11 +1,12 @@
 """The library's calls inside a captured CUDA graph: a sweep step (insert,
 fill with in-pass clearing, projection) captured twice -- the two
-accumulator sets swap at every step -- and replayed gives exactly the eager
-results, replay after replay."""
+accumulator sets swap at every step -- and replayed gives, replay after
+replay, exactly the CPU oracle's filled volume and projection (and the eager
+GPU results).  Host-pose insertion refuses to be captured."""
 import numpy as np
 import pytest
 
-from helpers import build_library
+from helpers import build_library, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -54,13 +55,38 @@ def test_sweep_step_replays_from_a_cuda_graph():
             vol.insert(imgs, poses, cal)
             vol.fill_and_clear()
             vol.project(lo, hi, out=out, count=cnt)
+    o = oracle_run(w)
+    assert np.array_equal(want_out.cpu().numpy(), o["proj"])
     for _ in range(3):
         out.zero_()
         cnt.zero_()
         g.replay()
         torch.cuda.synchronize()
-        assert torch.equal(out, want_out)
-        assert torch.equal(cnt, want_cnt)
+        assert np.array_equal(out.cpu().numpy(), o["proj"])
+        assert np.array_equal(cnt.cpu().numpy().view(np.uint16), o["pcnt"])
+        assert np.array_equal(vol.read(usvol.READ_VALUES).cpu().numpy(), o["val"])
+        assert np.array_equal(vol.read(usvol.READ_MASK).cpu().numpy(), o["has"])
+        assert torch.equal(out, want_out) and torch.equal(cnt, want_cnt)
         assert torch.equal(vol.read(usvol.READ_VALUES), want_val)
         assert not vol.read(usvol.READ_ACCUM).any()
     assert vol.status() == 0
+
+
+def test_host_pose_insert_is_refused_inside_a_capture():
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    w = synth.tiny_pnn(n=4, H=16, W=16)
+    vol = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+    imgs = torch.from_numpy(w.images).cuda()
+    cal = usvol.calibration_of(w)
+    vol.reset()
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    err = None
+    with torch.cuda.graph(g, stream=side):
+        try:
+            vol.insert(imgs, w.poses, cal)      # host poses
+        except usvol.UsvError as e:
+            err = e
+    assert err is not None and err.code == usvol.ERR_UNSUPPORTED

@@ -256,7 +256,7 @@ def test_argument_errors_with_a_live_volume():
 
     def ins(im=imgs.data_ptr(), n=2, H=16, W=16, dt=0, ps=poses.data_ptr(), c=cal):
         import ctypes
-        return L.usv_insert_frames(vol.handle, im, n, H, W, dt, ps, ctypes.byref(c), sp)
+        return L.usv_insert_frames_dev(vol.handle, im, n, H, W, dt, ps, ctypes.byref(c), sp)
 
     assert ins(n=-1) == usvol.ERR_ARG
     assert ins(H=0) == usvol.ERR_ARG
@@ -296,3 +296,35 @@ def test_whole_spine_full_size_bit_exact():
     o = oracle_run(w)
     assert g["status"] == 0 and o["skipped"] == 0
     assert_pnn_bit_exact(g, o)
+
+
+def test_host_poses_through_the_staging_ring_equal_device_poses_and_the_oracle():
+    """usv_insert_frames takes host poses (the tracker's output) and stages
+    them through the volume's pinned ring: calls of 4500 (two launches),
+    300, 1 and 199 frames, several times over so that the 2 MB ring wraps,
+    give exactly the volume of device-pose calls and of the oracle."""
+    import torch
+    from paper_2412_00058_gb300 import synth, usvol
+    w = synth.tiny_pnn(n=5000, H=16, W=32, sweep_mm=20.0)
+    imgs = torch.from_numpy(w.images).cuda()
+    cal = usvol.calibration_of(w)
+    a = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+    b = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
+    a.reset()
+    b.reset()
+    d_poses = torch.from_numpy(w.poses).cuda()
+    reps = 4                       # 4 x 640 KB of poses: the 2 MB ring wraps
+    for _ in range(reps):
+        f = 0
+        for k in (4500, 300, 1, 199):
+            a.insert(imgs[f:f + k], w.poses[f:f + k], cal)              # host poses
+            b.insert(imgs[f:f + k], d_poses[f:f + k], cal)              # device poses
+            f += k
+    assert a.status() == 0 and b.status() == 0
+    acc_a = a.read(usvol.READ_ACCUM).cpu().numpy().view(np.uint64)
+    assert np.array_equal(acc_a, b.read(usvol.READ_ACCUM).cpu().numpy().view(np.uint64))
+    import oracle
+    s, c, _ = oracle.insert_pnn(w.grid, w.images, w.poses, w.calib, w.sx, w.sy, w.spacing,
+                                w.origin)
+    assert np.array_equal(acc_a & np.uint64(0xFFFFFFFF), s * np.uint64(reps))
+    assert np.array_equal(acc_a >> np.uint64(32), c.astype(np.uint64) * np.uint64(reps))

@@ -397,3 +397,28 @@ def test_trilinear_fill_and_projection_closed_forms():
     assert not has[2, 2, 2]
     out, cnt = oracle.project_f64(val, has, 0, 3)
     assert cnt[1, 1] == 3 and math.isclose(out[1, 1], (60.0 + 16.5 + val[2, 1, 1]) / 3)
+
+
+def test_multi_core_oracle_gives_the_single_thread_bits():
+    """The OpenMP forms (frames split over host threads with atomic integer
+    adds; fill and projection split by plane / row) reproduce the plain
+    single-thread loops bit for bit."""
+    import oracle
+    from paper_2412_00058_gb300 import synth
+    w = synth.whole_spine(n=60, grid=(270, 80, 200), y_start_mm=3.0, y_span_mm=20.0)
+    cut = np.arange(w.n, dtype=np.int32) % 7 * 11
+    ref = []
+    try:
+        for t in (1, 4):
+            got = oracle.set_threads(t)
+            assert got == t or got == 1
+            s, c, sk = oracle.insert_pnn(w.grid, w.images, w.poses, w.calib, w.sx, w.sy,
+                                         w.spacing, w.origin, first_rows=cut)
+            v, h = oracle.fill_pnn(s, c)
+            p, pc = oracle.project_u8(v, h, *w.band)
+            ref.append((s, c, sk, v, h, p, pc))
+    finally:
+        oracle.set_threads(1)
+    for a, b in zip(*ref):
+        assert np.array_equal(a, b)
+    assert ref[0][1].sum() > 0
