@@ -597,12 +597,13 @@ def run_gpu(args):
         # the host link: the same bytes in one pinned host->device copy
         link = []
         le0, le1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(3):
-            le0.record(copy_stream)
-            d_imgs[1].copy_(h_imgs, non_blocking=True)
-            le1.record(copy_stream)
-            le1.synchronize()
-            link.append(h_imgs.numel() / (le0.elapsed_time(le1) / 1e3) / 1e9)
+        with torch.cuda.stream(copy_stream):
+            for _ in range(3):
+                le0.record(copy_stream)
+                d_imgs[1].copy_(h_imgs, non_blocking=True)
+                le1.record(copy_stream)
+                le1.synchronize()
+                link.append(h_imgs.numel() / (le0.elapsed_time(le1) / 1e3) / 1e9)
         link_gbs = max(link)
 
         def e2e_steps(k_steps):

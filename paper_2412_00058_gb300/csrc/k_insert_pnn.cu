@@ -8,23 +8,30 @@
 // GB300 design:
 //  * one CTA = a tile of TW columns x TH rows of FPC consecutive frames
 //    (default 128 x 64 x 8; TW is 64, 128 or 256, the shape is set per frame
-//    size or chosen by the autotuner); a row segment of TW pixels is TW/16
-//    lanes, each lane sixteen consecutive pixels read with one coalesced
-//    128-bit load (the next row's load is issued before the current row is
-//    processed).  With the default a quarter-warp covers one row and the
-//    CTA's 32 quarter-warps take every 32nd row.  The near-square tile keeps the box
-//    small: the frames are tilted in plane, and an axis-aligned box around a
-//    tilted 128 x 64 patch holds about 0.09 entries per pixel against 0.13
-//    for a 256 x 32 patch;
+//    size or chosen by the autotuner).  A row of the tile is cut into
+//    segments of 32 pixels, each read by one lane with two coalesced 16-byte
+//    loads (a whole 32-byte sector); the next wanted frame's segment is
+//    loaded while this one is inserted;
+//  * the lanes of a warp take segments of rows 4 apart (rows ordered 0, 4,
+//    8, ..., then 1, 5, ...): at 3 to 4 rows per voxel in depth, no two lanes
+//    of one step meet in a voxel, so a warp step's shared atomics do not
+//    serialise on one address;
 //  * the tile's voxel bounding box over its frames is exact (the map is
 //    affine, so the extremes sit at the tile corners), so the CTA can
 //    accumulate into a dense shared-memory box and then add each touched
-//    entry to HBM with one packed 64-bit global atomic;
-//  * per pixel: three exact 64-bit coordinate adds, the box index, one
-//    native 32-bit shared atomic.  In one step the lanes of a row segment
-//    handle pixels 16 columns apart (different voxels), so the atomics do
-//    not diverge; lanes of the warp's other rows may meet them in a voxel
-//    (a bank conflict, not a divergence);
+//    entry to HBM with one packed 64-bit global atomic.  Box rows are padded
+//    to 4 words and planes to 4 mod 8 words: 16-byte clears and flush loads,
+//    and the depth offsets of a warp's lanes fall on different banks;
+//  * per pixel (the inner loop is hand-written PTX, so the instruction mix
+//    is fixed): the box word from the three exact coordinates (two
+//    multiply-adds and a shift-add), one byte permute, one native 32-bit
+//    shared reduction, and the coordinate steps.  GB300's integer ALU and
+//    multiply-add units each take a warp instruction every other cycle, so
+//    the steps are split between them: x and z, when below half a voxel per
+//    pixel, advance by one wide multiply-add each (a 64-bit add of a
+//    sign-extended 32-bit step), y by a 64-bit add.  Where every lane of a
+//    warp stays in one y layer for its segment (frames tilted by a degree or
+//    less), y and its multiply-add drop out of the loop;
 //  * box entry layout: if the frames' bound on pixels per voxel (set-up
 //    kernel) keeps every count of the CTA below 1024, one word holds
 //    count (10 bits) | sum (22 bits) -> one atomic per pixel; otherwise
@@ -32,8 +39,10 @@
 //    shared memory (pixels as coarse as voxels, steep poses) every pixel
 //    goes straight to an HBM atomic;
 //  * bounds checks run only in tiles whose box was clipped by the grid, and
-//    there once per 16-pixel group: along a row every voxel index is monotone,
-//    so a group whose two end pixels are inside the box is inside.
+//    there once per segment: along a row every voxel index is monotone, so a
+//    segment whose two end pixels are inside the box is inside;
+//  * the flush takes the box 4 entries at a time (one 16-byte load), in row
+//    order, with exact multiply-high divisions for the row indices.
 #include <climits>
 
 #include "usv_internal.cuh"
@@ -43,19 +52,10 @@ namespace usv {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kPix = 16;             // pixels per lane per row (one 128-bit load)
-constexpr int kSmem = 48 * 1024;     // dynamic shared memory per CTA (the box)
+constexpr int kSeg = 32;             // pixels per lane segment (two 16-byte loads)
+constexpr int kSmem = 52 * 1024;     // dynamic shared memory per CTA (the box)
+constexpr int kBoxWords = kSmem / 4;
 constexpr int kMaxFpc = 8;           // frames per CTA (warp 0 takes 4 corners x 8 frames)
-
-// Tile geometry for a tile width TW (64, 128 or 256 columns): a row segment
-// of TW pixels is TW/8 lanes, so a warp covers 32/(TW/8) rows per pass.
-template <int TW>
-struct Tile {
-    static constexpr int kRowLanes = TW / kPix;            // lanes per row segment
-    static constexpr int kWarpRows = 32 / kRowLanes;       // rows per warp per pass
-    static constexpr int kPassRows = kWarps * kWarpRows;   // rows per CTA per pass
-};
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
 constexpr int kPackedMaxCount = 1023;
 
@@ -72,22 +72,7 @@ struct PnnArgs {
     int fpc;                // frames per CTA
 };
 
-__device__ __forceinline__ int hi32(long long q) { return (int)(q >> 32); }
-
-// Division by a CTA-uniform d in [1, 2^16] of numerators n < 2^16:
-// with m = floor(2^32 / d) + 1 = 2^32/d + e, 0 < e <= 1,
-//     n*m / 2^32 = n/d + n*e/2^32,   n*e/2^32 < 2^-16 <= 1/d,
-// and the fractional part of n/d is at most 1 - 1/d, so floor(n*m / 2^32)
-// = floor(n/d).  (d = 1 would need m = 2^32 + 1, so it is taken apart.)
-__device__ __forceinline__ unsigned div_magic(unsigned d)
-{
-    return d > 1u ? (unsigned)(0x100000000ull / d) + 1u : 0u;
-}
-
-__device__ __forceinline__ unsigned div_by(unsigned n, unsigned d, unsigned m)
-{
-    return d > 1u ? __umulhi(n, m) : n;
-}
+__device__ __forceinline__ unsigned hi32(long long q) { return (unsigned)(q >> 32); }
 
 __device__ __forceinline__ unsigned long long pack64(unsigned s, unsigned c)
 {
@@ -105,16 +90,56 @@ __device__ __forceinline__ unsigned byte_with(unsigned word, unsigned hi)
     return d;
 }
 
+// Box geometry of a CTA: extents and word strides.  Rows (fixed y, z) are
+// ex4 = ex rounded up to 4 words apart, planes zs words apart with
+// zs = 4 mod 8: the box is 16-byte aligned quad by quad (16-byte clears and
+// flush loads), and the depth offsets of a warp's lanes fall on 8 different
+// groups of 4 banks.
+struct Box {
+    unsigned ex, ey, ez, zs, ex4;
+};
+
+// 64-bit C + k*A for a 32-bit k: one wide multiply-add of A's low word and
+// one multiply-add of its high word into the result's high word (exact
+// modulo 2^64, which covers every map a valid frame can have).
+__device__ __forceinline__ long long mad64(unsigned k, long long A, long long C)
+{
+    long long d;
+    asm("{\n\t.reg .u32 dl, dh;\n\t"
+        "mad.wide.u32 %0, %1, %2, %3;\n\t"
+        "mov.b64 {dl, dh}, %0;\n\t"
+        "mad.lo.u32 dh, %1, %4, dh;\n\t"
+        "mov.b64 %0, {dl, dh};\n\t}"
+        : "=l"(d)
+        : "r"(k), "r"((unsigned)A), "l"(C), "r"((unsigned)((unsigned long long)A >> 32)));
+    return d;
+}
+
+// Division by a CTA-uniform d in [1, 2^16] of numerators n < 2^16:
+// with m = floor(2^32 / d) + 1 = 2^32/d + e, 0 < e <= 1,
+//     n*m / 2^32 = n/d + n*e/2^32,   n*e/2^32 < 2^-16 <= 1/d,
+// and the fractional part of n/d is at most 1 - 1/d, so floor(n*m / 2^32)
+// = floor(n/d).  (d = 1 would need m = 2^32 + 1, so it is taken apart.)
+__device__ __forceinline__ unsigned div_magic(unsigned d)
+{
+    return d > 1u ? (unsigned)(0x100000000ull / d) + 1u : 0u;
+}
+
+__device__ __forceinline__ unsigned div_by(unsigned n, unsigned d, unsigned m)
+{
+    return d > 1u ? __umulhi(n, m) : n;
+}
+
 // One pixel: box-local voxel from the coordinates, then the accumulate.
 template <bool CHECK, int MODE, int B>
 __device__ __forceinline__ void put(unsigned *box, unsigned cap, unsigned long long *acc,
-                                    long long qx, long long qy, long long qz, unsigned ex,
-                                    unsigned ey, unsigned ez, unsigned word)
+                                    long long qx, long long qy, long long qz, const Box &bx,
+                                    unsigned word)
 {
-    const unsigned lx = (unsigned)hi32(qx), ly = (unsigned)hi32(qy), lz = (unsigned)hi32(qz);
-    if (CHECK && !(lx < ex && ly < ey && lz < ez))
+    const unsigned lx = hi32(qx), ly = hi32(qy), lz = hi32(qz);
+    if (CHECK && !(lx < bx.ex && ly < bx.ey && lz < bx.ez))
         return;
-    const unsigned key = (lz * ey + ly) * ex + lx;
+    const unsigned key = lz * bx.zs + ly * bx.ex4 + lx;
     if (MODE == MODE_PACKED) {
         atomicAdd(box + key, byte_with<B>(word, 1u << kCountShift));
     } else if (MODE == MODE_SPLIT) {
@@ -125,111 +150,253 @@ __device__ __forceinline__ void put(unsigned *box, unsigned cap, unsigned long l
     }
 }
 
-template <int J, bool CHECK, int MODE>
-__device__ __forceinline__ void put_px(unsigned *box, unsigned cap, unsigned long long *acc,
-                                       long long qx, long long qy, long long qz, long long Ax,
-                                       long long Ay, long long Az, unsigned ex, unsigned ey,
-                                       unsigned ez, uint4 w, int npx)
+// The pixels [J, NPX) of a segment, Q stepping by A per pixel.
+template <int J, int NPX, bool CHECK, int MODE>
+__device__ __forceinline__ void put_run(unsigned *box, unsigned cap, unsigned long long *acc,
+                                        long long qx, long long qy, long long qz, long long Ax,
+                                        long long Ay, long long Az, const Box &bx, uint4 w0,
+                                        uint4 w1)
 {
-    if constexpr (J < kPix) {
-        if (J < npx)
-            put<CHECK, MODE, J & 3>(box, cap, acc, qx, qy, qz, ex, ey, ez,
-                                    J < 4 ? w.x : J < 8 ? w.y : J < 12 ? w.z : w.w);
-        put_px<J + 1, CHECK, MODE>(box, cap, acc, qx + Ax, qy + Ay, qz + Az, Ax, Ay, Az, ex, ey,
-                                   ez, w, npx);
+    if constexpr (J < NPX) {
+        constexpr int k = J & 15;
+        const uint4 &w = J < 16 ? w0 : w1;
+        const unsigned word = k < 4 ? w.x : k < 8 ? w.y : k < 12 ? w.z : w.w;
+        put<CHECK, MODE, J & 3>(box, cap, acc, qx, qy, qz, bx, word);
+        put_run<J + 1, NPX, CHECK, MODE>(box, cap, acc, qx + Ax, qy + Ay, qz + Az, Ax, Ay, Az,
+                                         bx, w0, w1);
     }
 }
 
-template <bool CHECK, int MODE>
-__device__ __forceinline__ void put_group(unsigned *box, unsigned cap, unsigned long long *acc,
-                                          long long qx, long long qy, long long qz, long long Ax,
-                                          long long Ay, long long Az, unsigned ex, unsigned ey,
-                                          unsigned ez, uint4 w, int npx)
+// A segment of npx pixels (VEC: 16 or 32) starting at Q.
+template <bool VEC, bool CHECK, int MODE>
+__device__ __forceinline__ void put_segment(unsigned *box, unsigned cap, unsigned long long *acc,
+                                            long long qx, long long qy, long long qz,
+                                            long long Ax, long long Ay, long long Az,
+                                            const Box &bx, uint4 w0, uint4 w1, int npx)
 {
-    put_px<0, CHECK, MODE>(box, cap, acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w, npx);
-}
-
-template <int TW, bool VEC, bool CHECK, int MODE>
-__device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int u0, int u1,
-                                           int v0, int v1, const long long (&off)[3],
-                                           unsigned ex, unsigned ey, unsigned ez, unsigned *box,
-                                           unsigned cap, const FrameRec *recs)
-{
-    constexpr int kRowLanes = Tile<TW>::kRowLanes, kWarpRows = Tile<TW>::kWarpRows;
-    constexpr int kPassRows = Tile<TW>::kPassRows;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int u = u0 + kPix * (lane % kRowLanes);
-    const int vs = v0 + warp * kWarpRows + lane / kRowLanes;  // this lane's first row
-    if (u >= u1 || vs >= v1)
-        return;
-    const int npx = VEC ? kPix : min(kPix, u1 - u);
-    const size_t rstep = (size_t)kPassRows * a.W;
-    for (int f = f0; f < f1; ++f) {
-        const FrameRec *r = recs + (f - f0);
-        if (!r->valid)
-            continue;
-        const long long Ax = r->q[0], Ay = r->q[1], Az = r->q[2];
-        const long long Bx = r->q[3], By = r->q[4], Bz = r->q[5];
-        // rows above first_row are cut away (tissue segmentation)
-        const int fr = r->first_row;
-        if (fr >= v1)
-            continue;
-        int v = vs;
-        if (v < fr)
-            v += (fr - v + kPassRows - 1) / kPassRows * kPassRows;
-        if (v >= v1)
-            continue;
-        const long long qx0 = r->q[6] + off[0] + (long long)u * Ax + (long long)v * Bx;
-        const long long qy0 = r->q[7] + off[1] + (long long)u * Ay + (long long)v * By;
-        const long long qz0 = r->q[8] + off[2] + (long long)u * Az + (long long)v * Bz;
-        const long long Rx = kPassRows * Bx, Ry = kPassRows * By, Rz = kPassRows * Bz;
-        const long long Ex = (kPix - 1) * Ax, Ey = (kPix - 1) * Ay, Ez = (kPix - 1) * Az;
-        long long qx = qx0, qy = qy0, qz = qz0;
-        const uint8_t *src = a.img + ((size_t)f * a.H + v) * a.W + u;
-        auto load = [&](const uint8_t *p) {
-            uint4 w;
-            if (VEC) {
-                w = __ldcs(reinterpret_cast<const uint4 *>(p));
-            } else {
-                w = make_uint4(0u, 0u, 0u, 0u);
-                for (int j = 0; j < npx; ++j) {
-                    const unsigned b = __ldcs(p + j) << (8 * (j & 3));
-                    if (j < 4)
-                        w.x |= b;
-                    else if (j < 8)
-                        w.y |= b;
-                    else if (j < 12)
-                        w.z |= b;
-                    else
-                        w.w |= b;
+    if (VEC) {
+        if (npx == kSeg)
+            put_run<0, 32, CHECK, MODE>(box, cap, acc, qx, qy, qz, Ax, Ay, Az, bx, w0, w1);
+        else
+            put_run<0, 16, CHECK, MODE>(box, cap, acc, qx, qy, qz, Ax, Ay, Az, bx, w0, w1);
+    } else {
+        // scalar-loaded segment of 1..32 pixels: pixels past npx carry no data
+        // and are skipped one by one
+        unsigned wd[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int j = 0; j < kSeg; ++j) {
+            if (j < npx) {
+                const unsigned word = wd[j >> 2];
+                switch (j & 3) {
+                case 0: put<CHECK, MODE, 0>(box, cap, acc, qx, qy, qz, bx, word); break;
+                case 1: put<CHECK, MODE, 1>(box, cap, acc, qx, qy, qz, bx, word); break;
+                case 2: put<CHECK, MODE, 2>(box, cap, acc, qx, qy, qz, bx, word); break;
+                default: put<CHECK, MODE, 3>(box, cap, acc, qx, qy, qz, bx, word); break;
                 }
             }
-            return w;
-        };
-        uint4 w = load(src);
-        for (; v < v1; v += kPassRows) {
-            const bool more = v + kPassRows < v1;
-            uint4 wn = make_uint4(0u, 0u, 0u, 0u);
-            if (more)
-                wn = load(src + rstep);
+            qx += Ax;
+            qy += Ay;
+            qz += Az;
+        }
+    }
+}
+
+// 16 pixels of one 16-byte load in hand-written PTX: per pixel the box word
+// address from the three exact coordinates (two multiply-adds and a
+// shift-add), the packed entry (one byte permute), one shared reduction, and
+// the three 64-bit coordinate steps.  Box-local coordinates, no checks.
+#define USV_PIX(W, B)                                                          \
+    "mov.b64 {lo, lx}, %0;\n\t"                                                \
+    "mov.b64 {lo, ly}, %1;\n\t"                                                \
+    "mov.b64 {lo, lz}, %2;\n\t"                                                \
+    "mad.lo.u32 t, ly, %10, %12;\n\t"                                          \
+    "mad.lo.u32 t, lz, %11, t;\n\t"                                            \
+    "shl.b32 ad, lx, 2;\n\t"                                                   \
+    "add.u32 ad, ad, t;\n\t"                                                   \
+    "prmt.b32 val, " W ", %13, " B ";\n\t"                                     \
+    "red.shared.add.u32 [ad], val;\n\t"                                        \
+    "add.s64 %0, %0, %3;\n\t"                                                  \
+    "add.s64 %1, %1, %4;\n\t"                                                  \
+    "add.s64 %2, %2, %5;\n\t"
+#define USV_WORD(W) USV_PIX(W, "0x7650") USV_PIX(W, "0x7651") USV_PIX(W, "0x7652") USV_PIX(W, "0x7653")
+
+// The same 16 pixels when the x and z steps are below half a voxel per
+// pixel: then each step fits a signed 32-bit word and pixel j's x and z
+// coordinates are one exact wide multiply-add from the segment start,
+// q(j) = q0 + j*A, instead of a chain of 64-bit adds (half the issue slots,
+// and the multiply-adds balance the integer units against the adds of y).
+#define USV_PIXW(W, B)                                                         \
+    "mov.b64 {lo, lx}, %0;\n\t"                                                \
+    "mov.b64 {lo, ly}, %1;\n\t"                                                \
+    "mov.b64 {lo, lz}, %2;\n\t"                                                \
+    "mad.lo.u32 t, ly, %10, %12;\n\t"                                          \
+    "mad.lo.u32 t, lz, %11, t;\n\t"                                            \
+    "shl.b32 ad, lx, 2;\n\t"                                                   \
+    "add.u32 ad, ad, t;\n\t"                                                   \
+    "prmt.b32 val, " W ", %13, " B ";\n\t"                                     \
+    "red.shared.add.u32 [ad], val;\n\t"                                        \
+    "mad.wide.s32 %0, %3, 1, %0;\n\t"                                          \
+    "add.s64 %1, %1, %4;\n\t"                                                  \
+    "mad.wide.s32 %2, %5, 1, %2;\n\t"
+#define USV_WORDW(W)                                                           \
+    USV_PIXW(W, "0x7650") USV_PIXW(W, "0x7651") USV_PIXW(W, "0x7652") USV_PIXW(W, "0x7653")
+
+// (x and z steps as 64-bit adds of a sign-extended 32-bit step: one wide
+// multiply-add by 1 each, on the multiply-add units, instead of two adds)
+__device__ __forceinline__ void put16_packed_w(long long &qx, long long &qy, long long &qz,
+                                               int Ax, long long Ay, int Az, uint4 w,
+                                               unsigned ex4, unsigned zs4, unsigned sbase)
+{
+    asm volatile("{\n\t.reg .u32 lo, lx, ly, lz, t, ad, val;\n\t"
+                 USV_WORDW("%6") USV_WORDW("%7") USV_WORDW("%8") USV_WORDW("%9")
+                 "}"
+                 : "+l"(qx), "+l"(qy), "+l"(qz)
+                 : "r"(Ax), "l"(Ay), "r"(Az), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w), "r"(ex4),
+                   "r"(zs4), "r"(sbase), "r"(1u << kCountShift)
+                 : "memory");
+}
+
+// 16 pixels of a segment that stays in one y layer: x and z only, the y
+// layer's offset (ybase, bytes, with the box base) fixed.
+#define USV_PIXF(W, B)                                                         \
+    "mov.b64 {lo, lx}, %0;\n\t"                                                \
+    "mov.b64 {lo, lz}, %1;\n\t"                                                \
+    "mad.lo.u32 t, lz, %8, %9;\n\t"                                            \
+    "shl.b32 ad, lx, 2;\n\t"                                                   \
+    "add.u32 ad, ad, t;\n\t"                                                   \
+    "prmt.b32 val, " W ", %10, " B ";\n\t"                                     \
+    "red.shared.add.u32 [ad], val;\n\t"                                        \
+    "mad.wide.s32 %0, %2, 1, %0;\n\t"                                          \
+    "mad.wide.s32 %1, %3, 1, %1;\n\t"
+#define USV_WORDF(W)                                                           \
+    USV_PIXF(W, "0x7650") USV_PIXF(W, "0x7651") USV_PIXF(W, "0x7652") USV_PIXF(W, "0x7653")
+
+__device__ __forceinline__ void put16_packed_xz(long long &qx, long long &qz, int Ax, int Az,
+                                                uint4 w, unsigned zs4, unsigned ybase)
+{
+    asm volatile("{\n\t.reg .u32 lo, lx, lz, t, ad, val;\n\t"
+                 USV_WORDF("%4") USV_WORDF("%5") USV_WORDF("%6") USV_WORDF("%7")
+                 "}"
+                 : "+l"(qx), "+l"(qz)
+                 : "r"(Ax), "r"(Az), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w), "r"(zs4),
+                   "r"(ybase), "r"(1u << kCountShift)
+                 : "memory");
+}
+
+__device__ __forceinline__ void put16_packed(long long &qx, long long &qy, long long &qz,
+                                             long long Ax, long long Ay, long long Az, uint4 w,
+                                             unsigned ex4, unsigned zs4, unsigned sbase)
+{
+    asm volatile("{\n\t.reg .u32 lo, lx, ly, lz, t, ad, val;\n\t"
+                 USV_WORD("%6") USV_WORD("%7") USV_WORD("%8") USV_WORD("%9")
+                 "}"
+                 : "+l"(qx), "+l"(qy), "+l"(qz)
+                 : "l"(Ax), "l"(Ay), "l"(Az), "r"(w.x), "r"(w.y), "r"(w.z), "r"(w.w), "r"(ex4),
+                   "r"(zs4), "r"(sbase), "r"(1u << kCountShift)
+                 : "memory");
+}
+
+template <bool VEC>
+__device__ __forceinline__ void load_segment(const uint8_t *p, int npx, uint4 &w0, uint4 &w1)
+{
+    if (VEC) {
+        w0 = __ldcs(reinterpret_cast<const uint4 *>(p));
+        w1 = npx > 16 ? __ldcs(reinterpret_cast<const uint4 *>(p) + 1) : make_uint4(0, 0, 0, 0);
+    } else {
+        unsigned wd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int j = 0; j < npx; ++j)
+            wd[j >> 2] |= (unsigned)__ldcs(p + j) << (8 * (j & 3));
+        w0 = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+        w1 = make_uint4(wd[4], wd[5], wd[6], wd[7]);
+    }
+}
+
+// All of the CTA's segments of all its frames, in one box mode.
+template <int TW, bool VEC, bool CHECK, int MODE>
+__device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u0, int u1,
+                                         int v0, int v1, const Box &bx, unsigned *box,
+                                         unsigned cap, const FrameRec *recs,
+                                         const long long (*q0)[3])
+{
+    constexpr int S = TW / kSeg;                 // segments per tile row
+    const int nrows = v1 - v0;
+    const int q = (nrows + 3) >> 2;              // rows per residue class mod 4
+    const int items = S * 4 * q;
+    for (int it = threadIdx.x; it < items; it += kThreads) {
+        const int s = it % S, rp = it / S;
+        const int r = 4 * (rp % q) + rp / q;     // consecutive lanes: rows 4 apart
+        const int u = u0 + kSeg * s;
+        if (r >= nrows || u >= u1)
+            continue;
+        const int v = v0 + r;
+        const int npx = VEC ? (u1 - u >= kSeg ? kSeg : 16) : min(kSeg, u1 - u);
+        const unsigned du = kSeg * s;
+        const uint8_t *row = a.img + (size_t)v * a.W + u;
+        const size_t fstride = (size_t)a.H * a.W;
+        // the frames of the group whose row v is inserted (valid, below the cut)
+        unsigned want = 0u;
+        for (int g = 0; g < f1 - f0; ++g)
+            want |= (recs[g].valid && v >= recs[g].first_row ? 1u : 0u) << g;
+        if (!want)
+            continue;
+        int f = __ffs(want) - 1;
+        want &= want - 1u;
+        uint4 w0, w1;
+        load_segment<VEC>(row + (size_t)(f0 + f) * fstride, npx, w0, w1);
+        for (;;) {
+            const int fn = want ? __ffs(want) - 1 : -1;
+            want &= want - 1u;
+            uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0;
+            if (fn >= 0)
+                load_segment<VEC>(row + (size_t)(f0 + fn) * fstride, npx, n0, n1);
+            const FrameRec *rr = recs + f;
+            const long long Ax = rr->q[0], Ay = rr->q[1], Az = rr->q[2];
+            const long long qx = mad64((unsigned)r, rr->q[3], mad64(du, Ax, q0[f][0]));
+            const long long qy = mad64((unsigned)r, rr->q[4], mad64(du, Ay, q0[f][1]));
+            const long long qz = mad64((unsigned)r, rr->q[5], mad64(du, Az, q0[f][2]));
             bool inside = true;
             if (CHECK) {
-                const long long lx = qx + Ex, ly = qy + Ey, lz = qz + Ez;
-                inside = (unsigned)hi32(qx) < ex && (unsigned)hi32(qy) < ey &&
-                         (unsigned)hi32(qz) < ez && (unsigned)hi32(lx) < ex &&
-                         (unsigned)hi32(ly) < ey && (unsigned)hi32(lz) < ez;
+                const long long e = npx - 1;
+                inside = hi32(qx) < bx.ex && hi32(qy) < bx.ey && hi32(qz) < bx.ez &&
+                         hi32(qx + e * Ax) < bx.ex && hi32(qy + e * Ay) < bx.ey &&
+                         hi32(qz + e * Az) < bx.ez;
             }
-            if (!CHECK || inside)
-                put_group<false, MODE>(box, cap, a.acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w,
-                                       npx);
+            if ((!CHECK || inside) && VEC && MODE == MODE_PACKED) {
+                long long x = qx, y = qy, z = qz;
+                const unsigned sbase = (unsigned)__cvta_generic_to_shared(box);
+                // steps below half a voxel: the wide multiply-add form
+                const bool narrow = Ax > -(1LL << 31) && Ax < (1LL << 31) &&
+                                    Az > -(1LL << 31) && Az < (1LL << 31);
+                // the segment stays in one y layer (and so, by the vote, does
+                // every lane of the warp here): two coordinates per pixel
+                const bool yc = hi32(qy) == hi32(qy + (long long)(npx - 1) * Ay);
+                if (narrow && __all_sync(__activemask(), yc) && yc) {
+                    const unsigned ybase = sbase + 4u * bx.ex4 * hi32(qy);
+                    put16_packed_xz(x, z, (int)Ax, (int)Az, w0, 4u * bx.zs, ybase);
+                    if (npx == kSeg)
+                        put16_packed_xz(x, z, (int)Ax, (int)Az, w1, 4u * bx.zs, ybase);
+                } else if (narrow) {
+                    put16_packed_w(x, y, z, (int)Ax, Ay, (int)Az, w0, 4u * bx.ex4, 4u * bx.zs,
+                                   sbase);
+                    if (npx == kSeg)
+                        put16_packed_w(x, y, z, (int)Ax, Ay, (int)Az, w1, 4u * bx.ex4,
+                                       4u * bx.zs, sbase);
+                } else {
+                    put16_packed(x, y, z, Ax, Ay, Az, w0, 4u * bx.ex4, 4u * bx.zs, sbase);
+                    if (npx == kSeg)
+                        put16_packed(x, y, z, Ax, Ay, Az, w1, 4u * bx.ex4, 4u * bx.zs, sbase);
+                }
+            } else if (!CHECK || inside)
+                put_segment<VEC, false, MODE>(box, cap, a.acc, qx, qy, qz, Ax, Ay, Az, bx, w0, w1,
+                                              npx);
             else
-                put_group<true, MODE>(box, cap, a.acc, qx, qy, qz, Ax, Ay, Az, ex, ey, ez, w,
-                                      npx);
-            qx += Rx;
-            qy += Ry;
-            qz += Rz;
-            src += rstep;
-            w = wn;
+                put_segment<VEC, true, MODE>(box, cap, a.acc, qx, qy, qz, Ax, Ay, Az, bx, w0, w1,
+                                             npx);
+            if (fn < 0)
+                break;
+            f = fn;
+            w0 = n0;
+            w1 = n1;
         }
     }
 }
@@ -240,9 +407,10 @@ __device__ __forceinline__ void run_frames(const PnnArgs &a, int f0, int f1, int
 template <int TW, bool VEC>
 __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int group)
 {
-    extern __shared__ unsigned box[];
-    __shared__ int s_lo[3], s_ext[3], s_mode, s_check;
+    extern __shared__ __align__(16) unsigned box[];
+    __shared__ int s_lo[3], s_ext[3], s_zs, s_ex4, s_mode, s_check;
     __shared__ FrameRec s_rec[kMaxFpc];
+    __shared__ long long s_q0[kMaxFpc][3];
 
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int u0 = tx * TW, v0 = ty * a.th;
@@ -280,10 +448,9 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
         const unsigned any = __reduce_or_sync(0xFFFFFFFFu, (unsigned)valid);
         const unsigned nsum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
         if (lane == 0) {
-            int mode = MODE_SKIP, check = 0;
+            int mode = MODE_SKIP, check = 0, zs = 0, ex4 = 0;
             if (any) {
                 const int n[3] = {a.nx, a.ny, a.nz};
-                long long vol = 1;
                 mode = MODE_PACKED;
                 for (int ax = 0; ax < 3; ++ax) {
                     const int l = max(lo[ax], 0), h = min(hi[ax], n[ax] - 1);
@@ -293,12 +460,17 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
                         check = 1;
                     s_lo[ax] = l;
                     s_ext[ax] = max(h - l + 1, 0);
-                    vol *= max(h - l + 1, 0);
                 }
                 if (mode != MODE_SKIP) {
-                    if (nsum <= kPackedMaxCount && vol <= kSmem / 4)
+                    // row stride: ex rounded up to 4; plane stride 4 mod 8
+                    ex4 = (s_ext[0] + 3) & ~3;
+                    long long z = (long long)ex4 * s_ext[1];
+                    z += (z & 4) ? 0 : 4;
+                    const long long words = z * s_ext[2];
+                    zs = (int)min(z, (long long)INT_MAX);
+                    if (nsum <= kPackedMaxCount && words <= kBoxWords)
                         mode = MODE_PACKED;
-                    else if (vol <= kSmem / 8)
+                    else if (words <= kBoxWords / 2)
                         mode = MODE_SPLIT;
                     else
                         mode = MODE_DIRECT;
@@ -306,75 +478,107 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
             }
             s_mode = mode;
             s_check = check;
+            s_zs = zs;
+            s_ex4 = ex4;
         }
     }
     __syncthreads();
     const int mode = s_mode;
     if (mode == MODE_SKIP)
         return;
-
+    // each frame's Q at the tile corner (u0, v0), box-local (or global for
+    // MODE_DIRECT), with the 2^31 of the rounding folded in
+    if (threadIdx.x < 3 * (f1 - f0)) {
+        const int fi = threadIdx.x / 3, ax = threadIdx.x % 3;
+        const FrameRec *r = s_rec + fi;
+        const long long off =
+            (1LL << 31) - (mode == MODE_DIRECT ? 0LL : ((long long)s_lo[ax] << 32));
+        s_q0[fi][ax] =
+            r->q[6 + ax] + (long long)u0 * r->q[ax] + (long long)v0 * r->q[3 + ax] + off;
+    }
     if (mode == MODE_DIRECT) {
+        __syncthreads();
         // keys are global linear indices into the whole grid
-        const long long off[3] = {1LL << 31, 1LL << 31, 1LL << 31};
-        run_frames<TW, VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, off, (unsigned)a.nx,
-                                           (unsigned)a.ny, (unsigned)a.nz, nullptr, 0, s_rec);
+        const Box g = {(unsigned)a.nx, (unsigned)a.ny, (unsigned)a.nz,
+                       (unsigned)a.nx * (unsigned)a.ny, (unsigned)a.nx};
+        run_tile<TW, VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, g, nullptr, 0, s_rec,
+                                             s_q0);
         return;
     }
-    const unsigned ex = s_ext[0], ey = s_ext[1], ez = s_ext[2];
-    const unsigned bvol = ex * ey * ez;
-    const unsigned cap = kSmem / 8;
-    for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
-        box[i] = 0u;
-        if (mode == MODE_SPLIT)
-            box[cap + i] = 0u;
+    const Box bx = {(unsigned)s_ext[0], (unsigned)s_ext[1], (unsigned)s_ext[2], (unsigned)s_zs,
+                    (unsigned)s_ex4};
+    const unsigned bwords = bx.zs * bx.ez;
+    const unsigned cap = kBoxWords / 2;
+    {
+        // 16-byte stores (every stride is a multiple of 4 words)
+        const unsigned quads = bwords / 4;
+        uint4 *b4 = reinterpret_cast<uint4 *>(box);
+        for (unsigned i = threadIdx.x; i < quads; i += kThreads) {
+            b4[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (mode == MODE_SPLIT)
+                b4[cap / 4 + i] = make_uint4(0u, 0u, 0u, 0u);
+        }
     }
     __syncthreads();
-    const long long off[3] = {(1LL << 31) - ((long long)s_lo[0] << 32),
-                              (1LL << 31) - ((long long)s_lo[1] << 32),
-                              (1LL << 31) - ((long long)s_lo[2] << 32)};
     if (mode == MODE_PACKED) {
         if (s_check)
-            run_frames<TW, VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box, 0,
-                                               s_rec);
+            run_tile<TW, VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, bx, box, 0, s_rec,
+                                                 s_q0);
         else
-            run_frames<TW, VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
-                                                0, s_rec);
+            run_tile<TW, VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, bx, box, 0, s_rec,
+                                                  s_q0);
     } else {
         if (s_check)
-            run_frames<TW, VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
-                                              cap, s_rec);
+            run_tile<TW, VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, bx, box, cap, s_rec,
+                                                s_q0);
         else
-            run_frames<TW, VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, off, ex, ey, ez, box,
-                                               cap, s_rec);
+            run_tile<TW, VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, bx, box, cap, s_rec,
+                                                 s_q0);
     }
     __syncthreads();
-    // Flush: the box in linear order, all threads busy; each touched entry
-    // goes to HBM with one packed 64-bit atomic.  Box coordinates come from
-    // the linear index by an exact multiply-high division (below).
-    const unsigned mx = div_magic(ex), my = div_magic(ey);
-    const size_t nxy = (size_t)a.nx * a.ny;
-    unsigned long long *base =
-        a.acc + ((size_t)s_lo[2] * a.ny + s_lo[1]) * a.nx + s_lo[0];
-    for (unsigned i = threadIdx.x; i < bvol; i += kThreads) {
-        const unsigned e = box[i];
-        unsigned s, c;
-        if (mode == MODE_PACKED) {
-            s = e & ((1u << kCountShift) - 1);
-            c = e >> kCountShift;
-        } else {
-            s = e;
-            c = box[cap + i];
-        }
-        if (c != 0u) {
-            const unsigned row = div_by(i, ex, mx), lx = i - row * ex;
-            const unsigned lz = div_by(row, ey, my), ly = row - lz * ey;
-            atomicAdd(base + lz * nxy + (size_t)ly * a.nx + lx, pack64(s, c));
+    // Flush: the threads take the box's quads (4 consecutive x entries of one
+    // (y, z) row) in row order; quad p is row p / qr, quad p % qr of it, the
+    // row (y, z) = (row % ey, row / ey), both by exact multiply-high
+    // division.  Each touched entry goes to HBM with one packed 64-bit
+    // atomic; the x padding of a row is never touched, so it is skipped as
+    // empty.
+    {
+        const unsigned qr = bx.ex4 / 4, nq = qr * bx.ey * bx.ez;
+        const unsigned mq = div_magic(qr), my = div_magic(bx.ey);
+        const size_t gplane = (size_t)a.nx * a.ny;
+        unsigned long long *gbase =
+            a.acc + ((size_t)s_lo[2] * a.ny + s_lo[1]) * a.nx + s_lo[0];
+        for (unsigned p = threadIdx.x; p < nq; p += kThreads) {
+            const unsigned row = div_by(p, qr, mq), qx4 = 4u * (p - row * qr);
+            const unsigned lz = div_by(row, bx.ey, my), ly = row - lz * bx.ey;
+            const unsigned off = lz * bx.zs + ly * bx.ex4 + qx4;
+            const uint4 e = *reinterpret_cast<const uint4 *>(box + off);
+            uint4 c4 = e;
+            if (mode != MODE_PACKED)
+                c4 = *reinterpret_cast<const uint4 *>(box + cap + off);
+            if ((e.x | e.y | e.z | e.w | c4.x | c4.y | c4.z | c4.w) == 0u)
+                continue;
+            unsigned long long *dst = gbase + lz * gplane + (size_t)ly * a.nx + qx4;
+            const unsigned ev[4] = {e.x, e.y, e.z, e.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                unsigned sv, cn;
+                if (mode == MODE_PACKED) {
+                    sv = ev[k] & ((1u << kCountShift) - 1);
+                    cn = ev[k] >> kCountShift;
+                } else {
+                    sv = ev[k];
+                    cn = cv[k];
+                }
+                if (cn != 0u)
+                    atomicAdd(dst + k, pack64(sv, cn));
+            }
         }
     }
 }
 
 template <int TW, bool VEC>
-__global__ void __launch_bounds__(kThreads) k_insert_pnn(PnnArgs a)
+__global__ void __launch_bounds__(kThreads, 4) k_insert_pnn(PnnArgs a)
 {
     insert_tile<TW, VEC>(a, blockIdx.x, blockIdx.y);
 }
@@ -391,7 +595,7 @@ struct PnnJobs {
     PnnArgs args[kMaxJobs];
 };
 
-__global__ void __launch_bounds__(kThreads) k_insert_pnn_multi(const __grid_constant__ PnnJobs J)
+__global__ void __launch_bounds__(kThreads, 4) k_insert_pnn_multi(const __grid_constant__ PnnJobs J)
 {
     const long long total = J.begin[J.njobs];
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
@@ -456,9 +660,10 @@ PnnArgs make_args(const Volume &v, const uint8_t *img, int n, int H, int W, cons
     return a;
 }
 
+// 16-byte loads need 16-byte rows and a 16-byte aligned first pixel.
 bool vec_ok(const uint8_t *img, int W)
 {
-    return (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
+    return (W % 16 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15) == 0);
 }
 
 }  // namespace
@@ -517,27 +722,15 @@ cudaError_t launch_insert_pnn(const Volume &v, const uint8_t *img, int n, int H,
         return cudaSuccess;
     if (!pnn_tile_ok(cfg))
         return cudaErrorInvalidValue;
-    PnnArgs a;
-    a.img = img;
-    a.n = n;
-    a.H = H;
-    a.W = W;
-    a.rec = v.rec;
-    a.acc = reinterpret_cast<unsigned long long *>(v.acc);
-    a.nx = v.g.nx;
-    a.ny = v.g.ny;
-    a.nz = v.g.nz;
-    a.th = min(cfg.tile_h, H);
-    a.tiles_x = (W + cfg.tile_w - 1) / cfg.tile_w;
+    PnnArgs a = make_args(v, img, n, H, W, cfg);
     const int tiles_y = (H + a.th - 1) / a.th;
     // frames_per_cta is an upper bound: a batch too small to fill the GPU's
-    // resident blocks (4 per SM at the 48 KB box) takes fewer frames per
+    // resident blocks (4 per SM at the 52 KB box) takes fewer frames per
     // block, down to one, so that more blocks share it
-    a.fpc = cfg.frames_per_cta;
     const long long resident = (long long)v.num_sms * 4;
     while (a.fpc > 1 && (long long)((n + a.fpc - 1) / a.fpc) * a.tiles_x * tiles_y < resident)
         a.fpc = (a.fpc + 1) / 2;
-    const bool vec = (W % kPix == 0) && ((reinterpret_cast<uintptr_t>(img) & (kPix - 1)) == 0);
+    const bool vec = vec_ok(img, W);
     const long long groups = (n + a.fpc - 1) / a.fpc;
     if (groups > 65535 || (long long)a.tiles_x * tiles_y > 0x7FFFFFFFLL)
         return cudaErrorInvalidConfiguration;

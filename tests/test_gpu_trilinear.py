@@ -69,10 +69,11 @@ def _carry_run(w, carry):
     from paper_2412_00058_gb300 import usvol
     vol = usvol.Volume(w.grid, w.spacing, w.origin, "trilinear")
     vol.reset()
-    usvol.insert_trilinear_carry(vol.handle, torch.from_numpy(w.images).cuda().data_ptr(), w.n,
-                                 w.H, w.W, usvol.F32 if w.images.dtype == np.float32 else usvol.U8,
-                                 torch.from_numpy(w.poses).cuda().data_ptr(),
-                                 usvol.calibration_of(w), carry)
+    imgs = torch.from_numpy(w.images).cuda()      # kept alive until the kernels have run
+    poses = torch.from_numpy(w.poses).cuda()
+    usvol.insert_trilinear_carry(vol.handle, imgs.data_ptr(), w.n, w.H, w.W,
+                                 usvol.F32 if w.images.dtype == np.float32 else usvol.U8,
+                                 poses.data_ptr(), usvol.calibration_of(w), carry)
     vol.fill()
     out, cnt = vol.project(*w.band)
     acc = vol.read(usvol.READ_ACCUM).cpu().numpy()
@@ -146,9 +147,9 @@ def _fan_frames_reaching(w, y0, y1):
 def test_convex_fan_full_size_slabs_against_oracle():
     """Full-size convex sweep (3000 frames of 512x512 into 400x1700x400) in
     the launch configuration of the timed path.  The oracle recomputes four
-    y-slabs of 12 voxel rows spread along the sweep -- its first rows (the
-    grid's y = 0 face, where tiles are clipped), two inner ones and its last
-    rows -- each from the frames that can reach it, on a sub-grid of the slab
+    y-slabs of 12 voxel rows spread along the sweep -- where it starts and
+    where it ends (only part of a frame group reaches them), and two inner
+    ones -- each from the frames that can reach it, on a sub-grid of the slab
     plus two rows each side (insertion into a sub-grid is exact for every
     voxel inside it).  The GPU's S, W, filled values and depth-band
     projection must match on each slab's rows, with the trilinear
@@ -162,7 +163,10 @@ def test_convex_fan_full_size_slabs_against_oracle():
     nx, ny, nz = w.grid
     lo, hi = w.band
     compared = 0
-    for y0 in (0, 420, 800, ny - 12):
+    # the rows where the sweep starts and ends, and two between
+    ys = [(w.poses[f] @ w.calib @ np.array([0.0, 0.0, 60.0, 1.0]))[1] for f in (0, w.n - 1)]
+    first, last = (int((y - w.origin[1]) / w.spacing[1]) for y in ys)
+    for y0 in (first - 6, 420, 800, last - 6):
         y1 = y0 + 12
         ya, yb = max(0, y0 - 2), min(ny, y1 + 2)
         keep = _fan_frames_reaching(w, ya, yb)
