@@ -334,11 +334,46 @@ def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
     step = float(np.median([t[0] for t in ts]))
     ins = float(np.median([t[1] for t in ts]))
     samples = w.n * w.H * w.W
+    # distinct voxels the sweep's one insertion launch touches (W > 0 after
+    # the last repetition's insert) and the insert's algorithmic bytes:
+    # 1 B per uint8 sample + 16 B per touched voxel (read + write of S, W)
+    vol.reset(stream)
+    vol.insert(imgs, poses, cal, stream)
+    acc = vol.read(usvol.READ_ACCUM, stream)
+    touched = int((acc[..., 1] > 0).sum().item())
+    del acc
+    peak, peak_kind = measured_peaks()
+    tri_bytes = samples * w.images.itemsize + 16 * touched
+    # the float2 vector-atomic ceiling: the library's probe, event-timed, into
+    # an L2-resident 64 MB buffer and a 2 GB one
+    ceil = {}
+    for label, nbytes in (("l2_64MB", 64 << 20), ("hbm_2GB", 2 << 30)):
+        buf = torch.zeros(nbytes // 4, dtype=torch.float32, device=dev)
+        reds = 64
+        nthreads = torch.cuda.get_device_properties(dev).multi_processor_count * 8 * 256
+        usvol.probe_red_f2(buf.data_ptr(), nbytes, reds, stream)   # warm-up
+        t_red = []
+        for _ in range(3):
+            ev[0].record(stream)
+            usvol.probe_red_f2(buf.data_ptr(), nbytes, reds, stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize(dev)
+            t_red.append(ev[0].elapsed_time(ev[1]))
+        ceil[label] = nthreads * reds / (min(t_red) / 1e3)
+        del buf
     out["trilinear_convex_sweep"] = {
         "workload": f"{w.n} convex frames 512x512 uint8 (60 deg, 120 mm) -> "
                     f"{w.grid[0]}x{w.grid[1]}x{w.grid[2]} @ 0.4 mm",
         "ms_per_sweep": step, "frames_per_s": w.n / step * 1e3,
-        "insert_ms": ins, "samples_per_s": samples / ins * 1e3, "tile": list(tri_tile)}
+        "insert_ms": ins, "samples_per_s": samples / ins * 1e3, "tile": list(tri_tile),
+        "touched_voxels": touched,
+        "roofline": {"bound": "hbm", "algorithmic_bytes": tri_bytes,
+                     "achieved": tri_bytes / (ins / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": tri_bytes / (ins / 1e3) / 1e9 / peak, "peak_kind": peak_kind},
+        "float2_atomic_ceiling_per_s": ceil,
+        "what": "algorithmic bytes = 1 B per uint8 sample + 16 B per voxel the launch touches; "
+                "the atomic ceilings are coalesced float2 reductions (usv_probe_red_f2) into an "
+                "L2-resident and an HBM-sized buffer"}
     del vol, imgs, poses
     torch.cuda.empty_cache()
     w = synth.pose_refine()
@@ -363,6 +398,32 @@ def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
         "workload": "512 FP32 frames 256x256 -> 256x512x192 @ 0.3 mm, band [80,140)",
         "ms_per_loss_and_gradient": float(np.median(ts)),
         "loss_at_noisy_poses": float(prob.loss.item())}
+
+    # refinement from the noisy poses toward the true poses' projection
+    def errors(P):
+        P = np.asarray(P).reshape(-1, 4, 4)
+        T = w.poses
+        t = np.abs(P[:, :3, 3] - T[:, :3, 3]).mean(axis=0)
+        R = np.einsum("fij,fkj->fik", P[:, :3, :3], T[:, :3, :3])
+        ang = np.degrees(np.arccos(np.clip((np.trace(R, axis1=1, axis2=2) - 1) / 2, -1, 1)))
+        return {"t_mm_xyz": [float(x) for x in t], "rot_deg": float(ang.mean())}
+    steps = 200
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    refined, hist = posegrad.refine(prob, steps=steps)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    out["pose_refinement"] = {
+        "workload": "the same 512 frames, poses perturbed by N(0, 1 mm) and N(0, 1 deg); target: "
+                    "the projection at the true poses",
+        "steps": steps, "loss_before": hist[0], "loss_after": hist[-1],
+        "mean_abs_error_before": errors(w.meta["noisy_poses"]),
+        "mean_abs_error_after": errors(refined.cpu().numpy()),
+        "ms_per_step": wall / steps * 1e3,
+        "what": "per-frame normalised descent steps with backtracking (posegrad.refine); each "
+                "step is one or more loss + gradient evaluations on the GPU plus host control; "
+                "x (lateral) and z (depth) are observed by the depth-band projection, y (along "
+                "the sweep) is not"}
     return out
 
 

@@ -465,6 +465,18 @@ int usv_test_insert_trilinear_carry(usv_volume *vol, const void *images_dev, int
                                     int32_t H, int32_t W, int32_t dtype, const double *poses_dev,
                                     const usv_calibration *cal, int32_t carry, void *stream);
 
+/* ------------------------------------------------------------------------
+ * usv_probe_red_f2 -- measurement utility (no counterpart in the paper):
+ * the ceiling the trilinear insertion's float2 vector atomics are measured
+ * against.  (num SMs x 8) blocks of 256 threads each add (1, 1) to
+ * reds_per_thread float2 entries of buf_dev ([bytes / 8] float2, 8-byte
+ * aligned, caller-owned; its contents grow): thread t of T takes entries
+ * (t + k*T) mod n, so a warp's reductions are one coalesced 256-byte run.
+ * Time it with events on `stream`; (T * reds_per_thread) / seconds is the
+ * reduction rate for that buffer size (L2-resident or not).
+ * ---------------------------------------------------------------------- */
+int usv_probe_red_f2(void *buf_dev, size_t bytes, int32_t reds_per_thread, void *stream);
+
 /* Synchronise `stream`, then return the device status bits (>= 0) and clear
  * them, or a negative USV_ERR_* code. */
 int usv_status(usv_volume *vol, void *stream);

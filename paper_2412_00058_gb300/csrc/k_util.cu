@@ -28,7 +28,31 @@ __global__ void __launch_bounds__(256) k_unpack_mask(const uint32_t *mask, uint8
     }
 }
 
+// Vector-atomic rate probe: thread t of T adds (1, 1) to float2 entries
+// (t + k*T) mod n for k < reds -- a warp's 32 reductions are one coalesced
+// 256-byte run, and the runs sweep the buffer.  With a buffer that fits in
+// L2 this is the L2's float2 reduction throughput; with one far larger than
+// L2 every reduction also reads and writes HBM.
+__global__ void __launch_bounds__(256) k_red_f2_probe(float2 *buf, unsigned long long n, int reds)
+{
+    const unsigned long long T = (unsigned long long)gridDim.x * blockDim.x;
+    unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int k = 0; k < reds; ++k) {
+        atomicAdd(buf + (i % n), make_float2(1.0f, 1.0f));
+        i += T;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_red_f2_probe(void *buf, size_t bytes, int reds, int num_sms, cudaStream_t st)
+{
+    const unsigned long long n = bytes / sizeof(float2);
+    if (n == 0 || reds <= 0)
+        return cudaSuccess;
+    k_red_f2_probe<<<(unsigned)num_sms * 8, 256, 0, st>>>(static_cast<float2 *>(buf), n, reds);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t st)
 {

@@ -1066,3 +1066,17 @@ int usv_test_insert_trilinear_carry(usv_volume *vol, const void *images_dev, int
     return usv::insert_impl(vol, images_dev, n, H, W, dtype, poses_dev, cal, nullptr, stream,
                             nullptr, nullptr, 8, carry != 0);
 }
+
+int usv_probe_red_f2(void *buf_dev, size_t bytes, int32_t reds_per_thread, void *stream)
+{
+    if (!buf_dev || (reinterpret_cast<uintptr_t>(buf_dev) & 7) != 0 || bytes < sizeof(float2) ||
+        reds_per_thread < 1)
+        return USV_ERR_ARG;
+    int dev = 0, sms = 0;
+    if (int rc = usv::cuda_rc(cudaGetDevice(&dev)))
+        return rc;
+    if (int rc = usv::cuda_rc(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+        return rc;
+    return usv::cuda_rc(usv::launch_red_f2_probe(buf_dev, bytes, reds_per_thread, sms,
+                                                 static_cast<cudaStream_t>(stream)));
+}

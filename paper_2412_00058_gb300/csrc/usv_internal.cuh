@@ -148,6 +148,7 @@ cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, c
 cudaError_t launch_project_f32(const Volume &v, int lo, int hi, const int *rlo, const int *rhi,
                                float *out, uint16_t *cnt, cudaStream_t st);
 cudaError_t launch_zero(void *p, size_t bytes, int num_sms, cudaStream_t st);
+cudaError_t launch_red_f2_probe(void *buf, size_t bytes, int reds, int num_sms, cudaStream_t st);
 cudaError_t launch_zero_f64(double *p, int n, cudaStream_t st);
 cudaError_t launch_soft_project_adjoint(const Volume &v, int lo, int hi, float eps,
                                         const float *target, float *proj, float2 *adj,

@@ -70,22 +70,30 @@ class PoseRefineLoss(torch.autograd.Function):
         return g * grad.to(g.dtype), None
 
 
-def refine(prob: PoseProblem, steps: int = 10, lr_t: float = 1e-6, lr_w: float = 1e-9,
-           backtrack: int = 6):
-    """Gradient descent on (t, w), re-linearised every step, with a
-    backtracking line search (the splat is only piecewise linear in the
-    poses, so a fixed step can overshoot a cell face): a step is halved up to
-    `backtrack` times until the loss does not increase, else skipped.
+def refine(prob: PoseProblem, steps: int = 200, step_t: float = 0.2, step_w: float = 0.003,
+           decay: float = 0.985, backtrack: int = 6):
+    """Descent on every frame's (t, w), re-linearised each step (the kernel's
+    gradient is exact at delta = 0).  Each frame moves along its own
+    gradient direction by a common length -- step_t mm for the
+    translation, step_w rad for the rotation, shrinking by `decay` per
+    step -- because the per-frame gradients differ by orders of magnitude
+    (frames that cross the band's bright bone against frames that do not).
+    The splat is only piecewise linear in the poses, so a step is halved up
+    to `backtrack` times until the loss does not increase, else skipped.
     Returns the refined poses and the loss after each step."""
     poses = prob.poses.clone()
     loss, grad = prob.evaluate(poses)
     hist = [float(loss.item())]
     saved = prob.poses
+    st, sw = step_t, step_w
     try:
         for _ in range(steps):
+            gt, gw = grad[:, :3], grad[:, 3:]
+            nt = gt.norm(dim=1, keepdim=True).clamp_min(1e-300)
+            nw = gw.norm(dim=1, keepdim=True).clamp_min(1e-300)
             scale = 1.0
             for _ in range(backtrack + 1):
-                delta = torch.cat([-scale * lr_t * grad[:, :3], -scale * lr_w * grad[:, 3:]], 1)
+                delta = torch.cat([-scale * st * gt / nt, -scale * sw * gw / nw], 1)
                 prob.poses = poses
                 cand = prob.perturbed(delta)
                 c_loss, c_grad = prob.evaluate(cand)
@@ -95,8 +103,12 @@ def refine(prob: PoseProblem, steps: int = 10, lr_t: float = 1e-6, lr_w: float =
                 scale *= 0.5
             else:
                 hist.append(hist[-1])
+                st *= decay
+                sw *= decay
                 continue
             hist.append(float(c_loss.item()))
+            st *= decay
+            sw *= decay
     finally:
         prob.poses = saved
     return poses, hist

@@ -39,7 +39,8 @@ EXPORTS = ("usv_volume_bytes", "usv_volume_create", "usv_volume_destroy", "usv_v
            "usv_bone_rows_alg2", "usv_pose_loss_grad", "usv_apply_pose_delta",
            "usv_fill_holes_and_clear", "usv_tune_insert", "usv_set_tile_config",
            "usv_get_tile_config", "usv_insert_frames_multi", "usv_test_fill_wait_timeout",
-           "usv_insert_frames_dev", "usv_frames_voxel_box", "usv_test_insert_trilinear_carry")
+           "usv_insert_frames_dev", "usv_frames_voxel_box", "usv_test_insert_trilinear_carry",
+           "usv_probe_red_f2")
 
 
 class UsvError(RuntimeError):
@@ -126,6 +127,8 @@ def lib():
             L.usv_test_insert_trilinear_carry.argtypes = [P, P, I, I, I, I, P,
                                                           ctypes.POINTER(Calibration), I, P]
             L.usv_test_insert_trilinear_carry.restype = ctypes.c_int
+            L.usv_probe_red_f2.argtypes = [P, Z, I, P]
+            L.usv_probe_red_f2.restype = ctypes.c_int
             L.usv_fill_holes.argtypes = [P, I, P]
             L.usv_fill_holes.restype = ctypes.c_int
             L.usv_project_depth_band.argtypes = [P, I, I, P, P, P]
@@ -300,6 +303,13 @@ def apply_pose_delta(poses_ptr: int, delta_ptr: int, n: int, H: int, W: int, cal
                                       W, ctypes.byref(cal), ctypes.c_void_p(out_ptr),
                                       ctypes.c_void_p(_stream_ptr(stream))),
            "usv_apply_pose_delta")
+
+
+def probe_red_f2(buf_ptr: int, nbytes: int, reds_per_thread: int, stream=None) -> None:
+    """Measurement utility: the float2 vector-atomic rate probe."""
+    _check(lib().usv_probe_red_f2(ctypes.c_void_p(buf_ptr), ctypes.c_size_t(nbytes),
+                                  int(reds_per_thread), ctypes.c_void_p(_stream_ptr(stream))),
+           "usv_probe_red_f2")
 
 
 def fill_holes(handle: int, radius: int = 1, stream=None) -> None:

@@ -208,6 +208,34 @@ def test_gpu_autograd_and_refinement_reduce_the_loss():
     loss.backward()
     _, grad = prob.evaluate(prob.poses)
     assert torch.allclose(delta.grad, grad)
-    _, hist = posegrad.refine(prob, steps=6, lr_t=2e-6, lr_w=2e-9)
+    _, hist = posegrad.refine(prob, steps=6)
     assert all(b <= a for a, b in zip(hist, hist[1:]))     # never accepts a worse loss
-    assert hist[-1] <= hist[0]
+    assert hist[-1] < hist[0]
+
+
+@pytest.mark.gpu
+def test_gpu_refinement_moves_noisy_poses_toward_the_truth():
+    """The pose-refinement workload's frame size, volume and band, 64
+    consecutive frames, poses perturbed by N(0, 1 mm) and N(0, 1 deg): 120
+    refinement steps against the projection of the true poses cut the loss
+    by 5x and the mean lateral (x) and depth (z) translation errors by a
+    quarter or more.  (The position along the sweep, y, is not observable
+    in a depth-band projection of frames that show the same anatomy, so it
+    is not asserted.)"""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    from helpers import build_library
+    from paper_2412_00058_gb300 import posegrad, synth
+    build_library()
+    n = 64
+    w = synth.pose_refine(n=n, sweep_mm=120.0 * (n - 1) / 511.0)
+    prob = _gpu_problem(w, w.meta["noisy_poses"], np.zeros((w.grid[1], w.grid[0])))
+    prob.evaluate(torch.from_numpy(w.poses).cuda())
+    prob.target = prob.proj.clone()
+    poses, hist = posegrad.refine(prob, steps=120)
+    err0 = np.abs(w.meta["noisy_poses"][:, :3, 3] - w.poses[:, :3, 3]).mean(axis=0)
+    err1 = np.abs(poses.cpu().numpy()[:, :3, 3] - w.poses[:, :3, 3]).mean(axis=0)
+    print("mean |t error| x, y, z (mm): before", err0, "after", err1, "loss", hist[0], hist[-1])
+    assert hist[-1] < 0.2 * hist[0]
+    assert err1[0] < 0.75 * err0[0] and err1[2] < 0.75 * err0[2]
