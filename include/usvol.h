@@ -59,6 +59,8 @@ extern "C" {
 #define USV_STATUS_BAD_POSE 0x1u   /* >= 1 frame skipped: non-affine pose, NaN/Inf or out of range */
 #define USV_STATUS_SATURATED 0x2u  /* >= 1 voxel count reached 2^24 (its sum may have wrapped)     */
 #define USV_STATUS_TIMEOUT 0x4u    /* a bounded device wait gave up                                 */
+#define USV_STATUS_OOB 0x8u        /* checked build only: a kernel write outside its buffer was
+                                      caught and skipped (a library bug; never set otherwise)     */
 
 typedef struct usv_volume usv_volume; /* opaque, host-side handle */
 

@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
             // this tile of plane z in the accumulators being cleared; every
             // voxel of the grid lies in exactly one (tile, plane)
             if (TMA) {
-                if (tid == 0) {
+                if (tid == 0 && guard(x0, a.nx, a.status) && guard(y0, a.ny, a.status) &&
+                    guard(z, a.nz, a.status)) {
                     tma_store_3d(&clear_map, x0, y0, z, zbase);
                     if (y0 + kZeroRows < a.ny)
                         tma_store_3d(&clear_map, x0, y0 + kZeroRows, z, zbase);
@@ -360,7 +361,8 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
             } else if (xin) {
                 unsigned long long *c = a.clear + ((size_t)z * a.ny + y0 + yb) * a.nx + x;
                 for (int r = 0; r < nrows; ++r)
-                    c[(size_t)r * a.nx] = 0ull;
+                    if (guard((c + (size_t)r * a.nx) - a.clear, plane * a.nz, a.status))
+                        c[(size_t)r * a.nx] = 0ull;
             }
         }
         if (z >= z0) {
@@ -405,10 +407,13 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
                         v = mean_round_u8(S, C);
                 }
                 const bool yin = r < nrows;
-                if (xin && yin)
+                if (xin && yin &&
+                    guard((vout + (size_t)r * a.nx) - val, plane * a.nz, a.status))
                     vout[(size_t)r * a.nx] = (uint8_t)v;
                 const unsigned bits = __ballot_sync(0xFFFFFFFFu, xin && yin && has);
-                if (tx == 0 && yin)
+                if (tx == 0 && yin &&
+                    guard((mout + (size_t)r * a.nxw) - a.mask,
+                          (size_t)a.nxw * a.ny * a.nz, a.status))
                     mout[(size_t)r * a.nxw] = bits;
             }
             vout += plane;
@@ -494,11 +499,13 @@ __global__ void __launch_bounds__(TX *TY) k_fill_f32(FillArgs a)
                 v = __fdiv_rn(S, W);
         }
         const size_t i = ((size_t)z * a.ny + y) * a.nx + x;
-        if (inside)
+        const size_t nvox = (size_t)a.nx * a.ny * a.nz;
+        if (inside && guard(i, nvox, a.status))
             val[i] = v;
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, inside && has);
-        if (tx == 0 && y < a.ny)
-            a.mask[((size_t)z * a.ny + y) * a.nxw + (x0 >> 5)] = bits;
+        const size_t mi = ((size_t)z * a.ny + y) * a.nxw + (x0 >> 5);
+        if (tx == 0 && y < a.ny && guard(mi, (size_t)a.nxw * a.ny * a.nz, a.status))
+            a.mask[mi] = bits;
         __syncthreads();
     }
 }

@@ -66,6 +66,7 @@ struct PnnArgs {
     int n, H, W;
     const FrameRec *rec;
     unsigned long long *acc;
+    uint32_t *status;       // checked build: USV_STATUS_OOB
     int nx, ny, nz;
     int th;                 // rows per tile
     int tiles_x;            // tiles per frame along u
@@ -97,6 +98,8 @@ __device__ __forceinline__ unsigned byte_with(unsigned word, unsigned hi)
 // groups of 4 banks.
 struct Box {
     unsigned ex, ey, ez, zs, ex4;
+    unsigned long long words;  // entries the keys may address (checked build)
+    uint32_t *status;
 };
 
 // 64-bit C + k*A for a 32-bit k: one wide multiply-add of A's low word and
@@ -140,6 +143,8 @@ __device__ __forceinline__ void put(unsigned *box, unsigned cap, unsigned long l
     if (CHECK && !(lx < bx.ex && ly < bx.ey && lz < bx.ez))
         return;
     const unsigned key = lz * bx.zs + ly * bx.ex4 + lx;
+    if (!guard(key, bx.words, bx.status))
+        return;
     if (MODE == MODE_PACKED) {
         atomicAdd(box + key, byte_with<B>(word, 1u << kCountShift));
     } else if (MODE == MODE_SPLIT) {
@@ -361,7 +366,7 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
                          hi32(qx + e * Ax) < bx.ex && hi32(qy + e * Ay) < bx.ey &&
                          hi32(qz + e * Az) < bx.ez;
             }
-            if ((!CHECK || inside) && VEC && MODE == MODE_PACKED) {
+            if (!kChecked && (!CHECK || inside) && VEC && MODE == MODE_PACKED) {
                 long long x = qx, y = qy, z = qz;
                 const unsigned sbase = (unsigned)__cvta_generic_to_shared(box);
                 // steps below half a voxel: the wide multiply-add form
@@ -500,13 +505,15 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
         __syncthreads();
         // keys are global linear indices into the whole grid
         const Box g = {(unsigned)a.nx, (unsigned)a.ny, (unsigned)a.nz,
-                       (unsigned)a.nx * (unsigned)a.ny, (unsigned)a.nx};
+                       (unsigned)a.nx * (unsigned)a.ny, (unsigned)a.nx,
+                       (unsigned long long)a.nx * a.ny * a.nz, a.status};
         run_tile<TW, VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, g, nullptr, 0, s_rec,
                                              s_q0);
         return;
     }
     const Box bx = {(unsigned)s_ext[0], (unsigned)s_ext[1], (unsigned)s_ext[2], (unsigned)s_zs,
-                    (unsigned)s_ex4};
+                    (unsigned)s_ex4,
+                    (unsigned long long)(unsigned)s_zs * (unsigned)s_ext[2], a.status};
     const unsigned bwords = bx.zs * bx.ez;
     const unsigned cap = kBoxWords / 2;
     {
@@ -570,7 +577,8 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
                     sv = ev[k];
                     cn = cv[k];
                 }
-                if (cn != 0u)
+                    if (cn != 0u && guard(qx4 + k, bx.ex, a.status) &&
+                    guard((dst + k) - a.acc, (unsigned long long)a.nx * a.ny * a.nz, a.status))
                     atomicAdd(dst + k, pack64(sv, cn));
             }
         }
@@ -651,6 +659,7 @@ PnnArgs make_args(const Volume &v, const uint8_t *img, int n, int H, int W, cons
     a.W = W;
     a.rec = v.rec;
     a.acc = reinterpret_cast<unsigned long long *>(v.acc);
+    a.status = v.status;
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;

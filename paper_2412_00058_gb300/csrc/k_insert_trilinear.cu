@@ -58,6 +58,7 @@ struct TriArgs {
     const FrameRec *rec;
     const double2 *beams;
     float2 *acc;
+    uint32_t *status;  // checked build: USV_STATUS_OOB
     int nx, ny, nz;
     int convex;
     double r0, dr;
@@ -149,9 +150,10 @@ __device__ __forceinline__ bool left_behind(int c, bool face, int abit, bool up)
 
 // Send a cell's corner terms to HBM, one vector atomic (S, W) per corner.
 template <bool CHECK>
-__device__ __forceinline__ void splat(float2 *acc, unsigned ex, unsigned ey, unsigned ez, int lx,
-                                      int ly, int lz, const float (&cS)[8], const float (&cW)[8],
-                                      bool face = false, int abit = 1, bool up = true)
+__device__ __forceinline__ void splat(float2 *acc, uint32_t *status, unsigned ex, unsigned ey,
+                                      unsigned ez, int lx, int ly, int lz, const float (&cS)[8],
+                                      const float (&cW)[8], bool face = false, int abit = 1,
+                                      bool up = true)
 {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -161,7 +163,9 @@ __device__ __forceinline__ void splat(float2 *acc, unsigned ex, unsigned ey, uns
         const unsigned X = (unsigned)(lx + cx), Y = (unsigned)(ly + cy), Z = (unsigned)(lz + cz);
         if (CHECK && !(X < ex && Y < ey && Z < ez))
             continue;
-        atomicAdd(acc + ((size_t)Z * ey + Y) * ex + X, make_float2(cS[c], cW[c]));
+        const size_t i = ((size_t)Z * ey + Y) * ex + X;
+        if (guard(X, ex, status) && guard(Y, ey, status) && guard(Z, ez, status))
+            atomicAdd(acc + i, make_float2(cS[c], cW[c]));
     }
 }
 
@@ -231,7 +235,8 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
                 const int abit = dx != 0 ? 1 : dy != 0 ? 2 : 4;
                 const bool up = dx + dy + dz > 0;
                 if (cx0 != INT_MIN)
-                    splat<CHECK>(a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW, face, abit, up);
+                    splat<CHECK>(a.acc, a.status, ex, ey, ez, cx0, cy0, cz0, cS, cW, face, abit,
+                                 up);
                 // new corner c is old corner c ^ abit when it receives: 0/1
                 // masks and multiply-adds (exact: one term is kept, the others
                 // are multiplied by zero) keep this off the integer pipe
@@ -283,7 +288,7 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
             }
         }
         if (cx0 != INT_MIN)
-            splat<CHECK>(a.acc, ex, ey, ez, cx0, cy0, cz0, cS, cW);
+            splat<CHECK>(a.acc, a.status, ex, ey, ez, cx0, cy0, cz0, cS, cW);
     }
 }
 
@@ -380,6 +385,7 @@ cudaError_t launch_insert_trilinear(const Volume &v, const void *img, int is_f32
     a.rec = v.rec;
     a.beams = v.beams;
     a.acc = static_cast<float2 *>(v.acc);
+    a.status = v.status;
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;

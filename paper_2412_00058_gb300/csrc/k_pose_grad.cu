@@ -48,6 +48,7 @@ struct SoftArgs {
     double *loss;
     int nx, ny, lo, hi;
     float eps;
+    uint32_t *status;   // checked build: USV_STATUS_OOB
 };
 
 __global__ void __launch_bounds__(256) k_soft_project_adjoint(SoftArgs a)
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(256) k_soft_project_adjoint(SoftArgs a)
             P += __fdiv_rn(sw.x, sw.y + a.eps);
         }
         P *= invB;
-        a.proj[i0] = P;
+        if (guard(i0, plane, a.status))
+            a.proj[i0] = P;
         const float d = P - a.target[i0];
         l = (double)d * (double)d;
         const float g = 2.0f * d * invB;
@@ -71,7 +73,9 @@ __global__ void __launch_bounds__(256) k_soft_project_adjoint(SoftArgs a)
             const float2 sw = a.acc[(size_t)z * plane + i0];
             const float den = sw.y + a.eps;
             const float gs = __fdiv_rn(g, den);
-            a.adj[(size_t)(z - a.lo) * plane + i0] = make_float2(gs, -gs * __fdiv_rn(sw.x, den));
+            const size_t ai = (size_t)(z - a.lo) * plane + i0;
+            if (guard(ai, (size_t)(a.hi - a.lo) * plane, a.status))
+                a.adj[ai] = make_float2(gs, -gs * __fdiv_rn(sw.x, den));
         }
     }
     // block reduction of the loss
@@ -96,6 +100,7 @@ struct GradArgs {
     const FrameRec *rec;
     const float2 *adj;
     double *grad;       // [n][6]: dL/dt (mm), dL/dw (rad)
+    uint32_t *status;   // checked build: USV_STATUS_OOB
     int nx, ny, nz, lo, hi;
     double s[3];        // voxel spacing (mm)
 };
@@ -207,7 +212,8 @@ __global__ void __launch_bounds__(256) k_pose_grad(GradArgs a, int tiles_x)
         double s = 0.0;
         for (int w = 0; w < 8; ++w)
             s += (double)part[w][threadIdx.x];
-        atomicAdd(a.grad + (size_t)f * 6 + threadIdx.x, s);
+        if (guard(f, a.n, a.status))
+            atomicAdd(a.grad + (size_t)f * 6 + threadIdx.x, s);
     }
 }
 
@@ -280,7 +286,7 @@ cudaError_t launch_soft_project_adjoint(const Volume &v, int lo, int hi, float e
                                         double *loss, cudaStream_t st)
 {
     SoftArgs a{static_cast<const float2 *>(v.acc), target, proj, adj, loss,
-               v.g.nx, v.g.ny, lo, hi, eps};
+               v.g.nx, v.g.ny, lo, hi, eps, v.status};
     dim3 grid((v.g.nx + 31) / 32, (v.g.ny + 7) / 8);
     k_soft_project_adjoint<<<grid, dim3(32, 8), 0, st>>>(a);
     return cudaGetLastError();
@@ -300,6 +306,7 @@ cudaError_t launch_pose_grad(const Volume &v, const void *img, int is_f32, int n
     a.rec = v.rec;
     a.adj = adj;
     a.grad = grad;
+    a.status = v.status;
     a.nx = v.g.nx;
     a.ny = v.g.ny;
     a.nz = v.g.nz;

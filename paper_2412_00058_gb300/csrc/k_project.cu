@@ -25,6 +25,7 @@ struct ProjArgs {
     uint16_t *cnt;
     int nx, ny, nxw, lo, hi;
     int rx0, ry0, rx1, ry1;  // refreshed columns [rx0, rx1) x [ry0, ry1)
+    uint32_t *status;        // checked build: USV_STATUS_OOB
 };
 
 __global__ void __launch_bounds__(256) k_project_u8(ProjArgs a)
@@ -57,6 +58,8 @@ __global__ void __launch_bounds__(256) k_project_u8(ProjArgs a)
         s += bit ? v : 0u;
         c += bit;
     }
+    if (!guard(i0, plane, a.status))
+        return;
     a.out[i0] = c ? __fdiv_rn((float)s, (float)c) : 0.0f;
     if (a.cnt)
         a.cnt[i0] = (uint16_t)c;
@@ -95,6 +98,8 @@ __global__ void __launch_bounds__(256) k_project_f32(ProjArgs a)
             c += 1;
         }
     }
+    if (!guard(i0, plane, a.status))
+        return;
     a.out[i0] = c ? __fdiv_rn(s, (float)c) : 0.0f;
     if (a.cnt)
         a.cnt[i0] = (uint16_t)c;
@@ -106,7 +111,7 @@ cudaError_t launch_project_u8(const Volume &v, int lo, int hi, const int *rlo, c
                               float *out, uint16_t *cnt, cudaStream_t st)
 {
     ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi,
-               rlo[0], rlo[1], rhi[0], rhi[1]};
+               rlo[0], rlo[1], rhi[0], rhi[1], v.status};
     dim3 grid((rhi[0] - rlo[0] + 31) / 32, (rhi[1] - rlo[1] + 7) / 8);
     if (grid.x == 0 || grid.y == 0)
         return cudaSuccess;
@@ -118,7 +123,7 @@ cudaError_t launch_project_f32(const Volume &v, int lo, int hi, const int *rlo, 
                                float *out, uint16_t *cnt, cudaStream_t st)
 {
     ProjArgs a{v.val, v.mask, out, cnt, v.g.nx, v.g.ny, v.nxw, lo, hi,
-               rlo[0], rlo[1], rhi[0], rhi[1]};
+               rlo[0], rlo[1], rhi[0], rhi[1], v.status};
     dim3 grid((rhi[0] - rlo[0] + 31) / 32, (rhi[1] - rlo[1] + 7) / 8);
     if (grid.x == 0 || grid.y == 0)
         return cudaSuccess;

@@ -9,6 +9,25 @@
 
 namespace usv {
 
+// Checked build (compiled with -DUSV_CHECKED): every global write and atomic
+// of the kernels, and every shared-memory accumulation, first tests its
+// index against the buffer it writes; an index outside is skipped and sets
+// USV_STATUS_OOB.  The regular build compiles the tests away.
+#ifdef USV_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool guard(unsigned long long idx, unsigned long long limit,
+                                      uint32_t *status)
+{
+    if (!kChecked || idx < limit)
+        return true;
+    atomicOr(status, USV_STATUS_OOB);
+    return false;
+}
+
 // Per-frame set-up record written by k_frame_setup (A0) into the volume's
 // scratch area and read by the insertion kernels.
 struct FrameRec {

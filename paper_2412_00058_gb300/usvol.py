@@ -20,10 +20,13 @@ import numpy as np
 import torch
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libusvol.so")
+# USV_CHECKED=1 in the environment loads the bounds-checked build, in which
+# every kernel write tests its index (an out-of-range one sets STATUS_OOB)
+CHECKED = os.environ.get("USV_CHECKED", "") == "1"
+LIB_PATH = os.path.join(_PKG, "libusvol_checked.so" if CHECKED else "libusvol.so")
 
 OK, ERR_ARG, ERR_RANGE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
-STATUS_BAD_POSE, STATUS_SATURATED, STATUS_TIMEOUT = 0x1, 0x2, 0x4
+STATUS_BAD_POSE, STATUS_SATURATED, STATUS_TIMEOUT, STATUS_OOB = 0x1, 0x2, 0x4, 0x8
 PNN, TRILINEAR = 0, 1
 SPARE_ACCUM = 0x100
 LINEAR, CONVEX = 0, 1
@@ -417,8 +420,12 @@ def volume_write_accum(handle: int, src_ptr: int, stream=None) -> None:
 
 
 def status(handle: int, stream=None) -> int:
-    return _check(lib().usv_status(ctypes.c_void_p(handle), ctypes.c_void_p(_stream_ptr(stream))),
+    bits = _check(lib().usv_status(ctypes.c_void_p(handle), ctypes.c_void_p(_stream_ptr(stream))),
                   "usv_status")
+    if bits & STATUS_OOB:
+        raise RuntimeError("the checked build caught a kernel write outside its buffer "
+                           f"(status {bits:#x})")
+    return bits
 
 
 # ---------------------------------------------------------------- convenience

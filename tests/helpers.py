@@ -6,8 +6,10 @@ import numpy as np
 
 
 def build_library():
-    from paper_2412_00058_gb300 import build
+    from paper_2412_00058_gb300 import build, usvol
     build.build()
+    if usvol.CHECKED:
+        build.build(checked=True)
     import oracle
     oracle.build()
 
