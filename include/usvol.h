@@ -106,7 +106,7 @@ typedef struct {
 /* ------------------------------------------------------------------------
  * usv_volume_bytes -- device bytes a volume needs: accumulators, filled
  * values, has-data bit mask, per-frame set-up scratch and the status word.
- * PNN: 8 B + 1 B + 1/8 B per voxel (+ ~0.6 MB); trilinear: 8 + 4 + 1/8;
+ * PNN: 8 B + 1 B + 1/8 B per voxel (+ ~1.2 MB); trilinear: 8 + 4 + 1/8;
  * with USV_SPARE_ACCUM in `mode`, 8 B more per voxel.
  * Returns 0 if the grid is invalid (any n < 1, or more than 2^31-1 voxels).
  * ---------------------------------------------------------------------- */
@@ -119,13 +119,16 @@ size_t usv_volume_bytes(usv_grid grid, int32_t mode);
  * owned by the caller and must outlive the handle.  spacing_mm > 0 and
  * finite; origin_mm finite (centre of voxel (0,0,0)).  The accumulators are
  * NOT cleared: call usv_volume_reset() before the first insert.
- * Allocates only the small host-side handle.
+ * Allocates the small host-side handle and the 2 MB pinned, device-mapped
+ * ring that stages host poses (usv_insert_frames); no device memory.
  * ---------------------------------------------------------------------- */
 int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double origin_mm[3],
                       int32_t mode, void *device_storage, size_t storage_bytes,
                       usv_volume **out);
 
-/* Frees the host handle only; the storage is the caller's. */
+/* Frees the host handle and its pose ring; the storage is the caller's.
+ * Waits on the host for the queued set-up kernels that still read poses
+ * from the ring, then frees it. */
 int usv_volume_destroy(usv_volume *vol);
 
 /* Zero the accumulators and the status word (start of a new scan). */
@@ -138,11 +141,14 @@ int usv_volume_reset(usv_volume *vol, void *stream);
  *   images_dev  [n][H][W] uint8 (USV_U8) or float32 (USV_F32), C-order.
  *   poses_host  [n][16] float64 probe->world matrices in host memory (the
  *               tracker's output, Sec. II.B), row-major; read during the
- *               call: they are copied into the volume's pinned staging ring
- *               (2 MB, allocated by usv_volume_create) and from there to the
- *               device on `stream`.  The call waits on the host only when
- *               the ring is still held by copies the device has not done yet
- *               (more than 2 MB of poses in flight).  Not allowed while
+ *               call: they are copied into the volume's pinned, device-
+ *               mapped staging ring (2 MB, allocated by usv_volume_create),
+ *               which the work queued on `stream` reads in place over the
+ *               host link (no copy-engine transfer, so the call never waits
+ *               behind the caller's own frame copies).  The call waits on
+ *               the host only when the ring is still held by work the
+ *               device has not done yet (more than 2 MB of poses, or 64
+ *               calls, in flight).  Not allowed while
  *               `stream` is being captured into a CUDA graph
  *               (USV_ERR_UNSUPPORTED): capture usv_insert_frames_dev().
  *   cal         host struct, read during the call only.

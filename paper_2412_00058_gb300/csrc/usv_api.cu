@@ -70,12 +70,15 @@ int cuda_rc(cudaError_t e)
 
 }  // namespace
 
-// Pinned host memory through which host-side poses reach the device: each
-// insertion launch copies its frames' poses (128 B per frame) into the ring,
-// then one asynchronous host->device copy on the caller's stream takes them
-// to the volume's device pose slot.  A region of the ring is written again
-// only after the copy that read it has completed (an event per region), so
-// the host can run several calls ahead of the device.
+// Pinned, device-mapped host memory through which host-side poses reach
+// the device: each insertion launch copies its frames' poses (128 B per
+// frame) into a region of the ring, and the frame set-up kernel reads them
+// from there over the host link.  No copy engine is involved: an
+// asynchronous host->device copy on the caller's stream would queue behind
+// the caller's own bulk frame copies on the copy engines and hold back the
+// insertion.  A region is written again only after the work that read it
+// has completed (an event per region), so the host can run several calls
+// ahead of the device.
 class PoseRing {
 public:
     static constexpr size_t kBytes = 2u << 20;  // 2 MB: four full launches of 4096 frames
@@ -84,13 +87,20 @@ public:
     cudaError_t init()
     {
         cudaError_t e = cudaHostAlloc(reinterpret_cast<void **>(&base_), kBytes,
-                                      cudaHostAllocDefault);
+                                      cudaHostAllocMapped);
+        void *dev = nullptr;
+        if (e == cudaSuccess)
+            e = cudaHostGetDevicePointer(&dev, base_, 0);
+        dev_ = static_cast<const char *>(dev);
         for (int i = 0; e == cudaSuccess && i < kMaxInFlight; ++i)
             e = cudaEventCreateWithFlags(&ev_[i], cudaEventDisableTiming);
         return e;
     }
     ~PoseRing()
     {
+        // the device may still be reading regions: wait for their readers
+        for (; count_ > 0; --count_, first_ = (first_ + 1) % kMaxInFlight)
+            cudaEventSynchronize(ev_[first_]);
         for (int i = 0; i < kMaxInFlight; ++i)
             if (ev_[i])
                 cudaEventDestroy(ev_[i]);
@@ -98,8 +108,9 @@ public:
             cudaFreeHost(base_);
     }
 
-    // Stage `bytes` (<= kBytes) from `src` and copy them to `dst_dev` on `st`.
-    cudaError_t stage(const void *src, size_t bytes, void *dst_dev, cudaStream_t st)
+    // Copy `bytes` (<= kBytes) from `src` into a free region and return its
+    // device address in *dev; fence() must follow once its reader is queued.
+    cudaError_t put(const void *src, size_t bytes, const void **dev)
     {
         size_t off = head_;
         if (off + bytes > kBytes)
@@ -113,17 +124,24 @@ public:
             --count_;
         }
         std::memcpy(base_ + off, src, bytes);
-        cudaError_t e = cudaMemcpyAsync(dst_dev, base_ + off, bytes, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess)
-            return e;
+        put_off_ = off;
+        put_bytes_ = bytes;
+        *dev = dev_ + off;
+        return cudaSuccess;
+    }
+
+    // The region of the last put() stays in use until the work queued on
+    // `st` so far has completed.
+    cudaError_t fence(cudaStream_t st)
+    {
         const int slot = (first_ + count_) % kMaxInFlight;
-        e = cudaEventRecord(ev_[slot], st);
+        cudaError_t e = cudaEventRecord(ev_[slot], st);
         if (e != cudaSuccess)
             return e;
-        use_off_[slot] = off;
-        use_bytes_[slot] = bytes;
+        use_off_[slot] = put_off_;
+        use_bytes_[slot] = put_bytes_;
         ++count_;
-        head_ = off + bytes;
+        head_ = put_off_ + put_bytes_;
         return cudaSuccess;
     }
 
@@ -134,7 +152,8 @@ private:
     }
 
     char *base_ = nullptr;
-    size_t head_ = 0;
+    const char *dev_ = nullptr;
+    size_t head_ = 0, put_off_ = 0, put_bytes_ = 0;
     cudaEvent_t ev_[kMaxInFlight] = {};
     size_t use_off_[kMaxInFlight] = {}, use_bytes_[kMaxInFlight] = {};
     int first_ = 0, count_ = 0;
@@ -156,8 +175,6 @@ Layout layout_for(usv_grid g, int mode)
     off += align_up((size_t)kRecCap * sizeof(FrameRec));
     L.beams = off;
     off += align_up((size_t)kBeamCap * sizeof(double2));
-    L.poses = off;
-    off += align_up((size_t)kRecCap * 16 * sizeof(double));
     L.status = off;
     off += kAlign;
     L.spare = 0;
@@ -249,7 +266,6 @@ int usv_volume_create(usv_grid grid, const double spacing_mm[3], const double or
     v->status = reinterpret_cast<uint32_t *>(v->base + L.status);
     v->num_sms = sms;
     v->device = attr.device;
-    v->pose_slot = reinterpret_cast<double *>(v->base + L.poses);
     v->ring = new (std::nothrow) usv::PoseRing();
     if (!v->ring) {
         delete v;
@@ -274,7 +290,7 @@ int usv_volume_destroy(usv_volume *vol)
     Volume *v = reinterpret_cast<Volume *>(vol);
     {
         usv::DeviceGuard g(v->device);
-        delete v->ring;  // waits for nothing: the caller's stream owns the pending copies
+        delete v->ring;  // waits for the set-up kernels that read the ring, then frees it
     }
     delete v;
     return USV_OK;
@@ -297,8 +313,8 @@ int usv_volume_reset(usv_volume *vol, void *stream)
 namespace usv {
 // acc_override / cfg_override: insert into other accumulators with a given
 // tile shape (the autotuner); null = the volume's own, tile_for().
-// poses_on_host: `poses` is host memory, staged through the volume's pinned
-// ring into its device pose slot launch by launch.
+// poses_on_host: `poses` is host memory, staged launch by launch through the
+// volume's pinned ring, which the set-up kernel reads in place.
 int insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t H, int32_t W,
                 int32_t dtype, const double *poses, const usv_calibration *cal,
                 const int32_t *first_rows_dev, void *stream, void *acc_override = nullptr,
@@ -608,12 +624,15 @@ int usv::insert_impl(usv_volume *vol, const void *images_dev, int32_t n, int32_t
         sp.first_rows = first_rows_dev ? first_rows_dev + c0 : nullptr;
         const double *pc = poses + (size_t)c0 * 16;
         if (poses_on_host) {
-            e = v.ring->stage(pc, (size_t)nc * 16 * sizeof(double), v.pose_slot, st);
+            const void *mapped = nullptr;
+            e = v.ring->put(pc, (size_t)nc * 16 * sizeof(double), &mapped);
             if (e != cudaSuccess)
                 break;
-            pc = v.pose_slot;
+            pc = static_cast<const double *>(mapped);
         }
         e = usv::launch_frame_setup(pc, nc, sp, v.rec, v.status, st);
+        if (e == cudaSuccess && poses_on_host)
+            e = v.ring->fence(st);  // the set-up kernel is the region's only reader
         if (e != cudaSuccess)
             break;
         const char *img = static_cast<const char *>(images_dev) + (size_t)c0 * frame_bytes;

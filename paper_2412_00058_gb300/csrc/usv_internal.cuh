@@ -75,8 +75,7 @@ struct Volume {
     int device;
     TunedTile tuned[kTunedCap];  // tile shapes set or tuned per frame size
     int ntuned;
-    double *pose_slot;  // device: poses of one insertion launch, copied from host poses
-    PoseRing *ring;     // host poses staged here before their copy (owned by the handle)
+    PoseRing *ring;     // host poses staged here, read in place (owned by the handle)
 };
 
 // The tile for frames of H x W in this volume: a tuned or set one, else the
@@ -90,7 +89,7 @@ constexpr int kBeamCap = 32768;    // max W
 constexpr int kMaxDim = 32768;     // max H, W
 
 struct Layout {
-    size_t acc, val, mask, rec, beams, poses, status, spare, total;  // spare: 0 if none
+    size_t acc, val, mask, rec, beams, status, spare, total;  // spare: 0 if none
 };
 Layout layout_for(usv_grid g, int mode);  // mode may carry USV_SPARE_ACCUM
 

@@ -1,6 +1,7 @@
 """bench.py prints one JSON line with the keys its consumers read: the CPU
-reference arm (the oracle on all host cores, the whole sweep every step;
-here a 600-frame piece of it) on the CPU, and a short GPU run on a 600-frame
+reference arm (the oracle on all host cores, the whole sweep every step, or
+a measured piece of it when K + W sweeps would pass the time budget; here
+on a 600-frame sweep) on the CPU, and a short GPU run on a 600-frame
 piece of the sweep on the GPU."""
 import json
 import os
@@ -34,6 +35,39 @@ def test_reference_arm_line():
     assert abs(d["ms_per_step"] - 600 / d["value"] * 1e3) < 1e-6 * d["ms_per_step"]
     assert d["e2e"] == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+    assert cb["frames_per_step"] == 600
+
+
+def test_reference_arm_bounds_long_runs_by_a_measured_piece():
+    """When K + W whole sweeps would pass the budget, a step is a piece of the
+    sweep, timed as it is: ms_per_step is the piece's own time."""
+    d = run_bench("--impl", "reference", "--steps", "3", "--warmup", "1", "--frames", "600",
+                  "--ref-budget-s", "0.05")
+    cb = d["cpu_baseline"]
+    m = cb["frames_per_step"]
+    assert 1 <= m < 600 and "measured, not scaled" in cb["sample"]
+    assert d["steps"] == 3 and d["value"] > 0
+    assert abs(d["ms_per_step"] - m / d["value"] * 1e3) < 1e-6 * d["ms_per_step"]
+
+
+def test_reference_piece_slab_holds_every_pixel_of_its_frames():
+    """The y-slab of a piece receives exactly what the full volume receives
+    from the same frames."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    w = bench.sweep_workload(300)
+    f0, m, grid, origin = bench.oracle_piece(w, 100, 60)
+    fr = slice(f0, f0 + m)
+    s_full, c_full, _ = oracle.insert_pnn(w.grid, w.images[fr], w.poses[fr], w.calib, w.sx,
+                                          w.sy, w.spacing, w.origin)
+    s, c, _ = oracle.insert_pnn(grid, w.images[fr], w.poses[fr], w.calib, w.sx, w.sy,
+                                w.spacing, origin)
+    y0 = int(round((origin[1] - w.origin[1]) / w.spacing[1]))
+    assert grid[1] < w.grid[1] and int(c.sum()) == int(c_full.sum()) > 0
+    assert np.array_equal(c, c_full[:, y0:y0 + grid[1], :])
+    assert np.array_equal(s, s_full[:, y0:y0 + grid[1], :])
 
 
 @pytest.mark.gpu
