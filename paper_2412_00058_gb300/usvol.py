@@ -545,6 +545,87 @@ class Volume:
     def status(self, stream=None) -> int:
         return status(self.handle, stream)
 
+    def save(self, path, stream=None) -> None:
+        """Write the accumulators (the raw integer sum/count pairs of PNN, the
+        FP32 (S, W) pairs of trilinear) and the geometry to `path`, so that a
+        scan can be resumed bit-exactly with Volume.load (the paper stores
+        its volume at the end of a scan, Sec. II.C)."""
+        acc = self.read(READ_ACCUM, stream).cpu().numpy()
+        write_volume_file(path, dict(grid=list(self.grid), spacing=list(self.spacing),
+                                     origin=list(self.origin), mode=_MODE_NAMES[self.mode]), acc)
+
+    @classmethod
+    def load(cls, path, device="cuda", spare=False, stream=None) -> "Volume":
+        """A volume with the geometry and accumulators saved by Volume.save;
+        its filled values are not restored (run fill() again)."""
+        meta, acc = read_volume_file(path)
+        vol = cls(meta["grid"], meta["spacing"], meta["origin"], meta["mode"], device=device,
+                  spare=spare)
+        src = torch.from_numpy(acc).to(vol.storage.device)
+        volume_write_accum(vol.handle, src.data_ptr(), stream)
+        # the host copy must stay alive until the stream-ordered write is done
+        (torch.cuda.current_stream(vol.storage.device) if stream is None else stream).synchronize()
+        return vol
+
+    def save_slices(self, directory, stream=None) -> list:
+        """Write the filled volume as one 8-bit greyscale image per slice along
+        the spine axis (y), depth down and lateral across, as binary PGM files
+        (the paper's end-of-scan output, Sec. II.C).  Trilinear values are
+        rounded and clamped to [0, 255].  Returns the file names."""
+        vals = self.read(READ_VALUES, stream).cpu().numpy()          # [nz, ny, nx]
+        if vals.dtype != np.uint8:
+            vals = np.clip(np.rint(vals), 0, 255).astype(np.uint8)
+        os.makedirs(directory, exist_ok=True)
+        nz, ny, nx = vals.shape
+        names = []
+        for y in range(ny):
+            name = os.path.join(directory, f"slice_{y:05d}.pgm")
+            with open(name, "wb") as f:
+                f.write(b"P5\n%d %d\n255\n" % (nx, nz))
+                f.write(np.ascontiguousarray(vals[:, y, :]).tobytes())
+            names.append(name)
+        return names
+
+
+_MODE_NAMES = {PNN: "pnn", TRILINEAR: "trilinear"}
+_FILE_MAGIC = b"USVOLACC"
+
+
+def write_volume_file(path, meta: dict, acc: np.ndarray) -> None:
+    """The saved-volume format: 8 magic bytes, a 4-byte little-endian header
+    length, a UTF-8 JSON header (geometry, mode, dtype, shape) and the raw
+    accumulator array in C order."""
+    import json
+    head = dict(meta, dtype=str(acc.dtype), shape=list(acc.shape), version=1)
+    hb = json.dumps(head, sort_keys=True).encode()
+    with open(path, "wb") as f:
+        f.write(_FILE_MAGIC)
+        f.write(len(hb).to_bytes(4, "little"))
+        f.write(hb)
+        f.write(np.ascontiguousarray(acc).tobytes())
+
+
+def read_volume_file(path):
+    """(header dict, accumulator array) of a file written by write_volume_file;
+    raises ValueError on a foreign, truncated or inconsistent file."""
+    import json
+    with open(path, "rb") as f:
+        if f.read(8) != _FILE_MAGIC:
+            raise ValueError(f"{path}: not a saved volume")
+        n = int.from_bytes(f.read(4), "little")
+        head = json.loads(f.read(n).decode())
+        data = f.read()
+    if head.get("version") != 1 or head.get("mode") not in ("pnn", "trilinear"):
+        raise ValueError(f"{path}: unsupported header {head}")
+    nx, ny, nz = head["grid"]
+    want = [nz, ny, nx] + ([2] if head["mode"] == "trilinear" else [])
+    dt = np.dtype(head["dtype"])
+    if head["shape"] != want or dt != (np.int64 if head["mode"] == "pnn" else np.float32):
+        raise ValueError(f"{path}: accumulator shape/dtype do not match the grid")
+    if len(data) != int(np.prod(want)) * dt.itemsize:
+        raise ValueError(f"{path}: truncated accumulators")
+    return head, np.frombuffer(data, dtype=dt).reshape(want).copy()
+
 
 def calibration_of(w) -> Calibration:
     """Calibration struct for a synth.Workload (or any object with the same fields)."""
