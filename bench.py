@@ -343,7 +343,7 @@ def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
     nx, ny, nz = w.grid
     img_out = torch.empty((ny, nx), dtype=torch.float32, device=dev)
     cnt = torch.empty((ny, nx), dtype=torch.int16, device=dev)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
     ts = []
     for r in range(reps + 1):
         ev[0].record(stream)
@@ -352,13 +352,18 @@ def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
         vol.insert(imgs, poses, cal, stream)
         ev[2].record(stream)
         vol.fill(stream)
-        vol.project(*w.band, out=img_out, count=cnt, stream=stream)
         ev[3].record(stream)
+        vol.project(*w.band, out=img_out, count=cnt, stream=stream)
+        ev[4].record(stream)
         torch.cuda.synchronize(dev)
         if r:
-            ts.append((ev[0].elapsed_time(ev[3]), ev[1].elapsed_time(ev[2])))
-    step = float(np.median([t[0] for t in ts]))
-    ins = float(np.median([t[1] for t in ts]))
+            ts.append([ev[0].elapsed_time(ev[4])] +
+                      [ev[k].elapsed_time(ev[k + 1]) for k in range(4)])
+    med = [float(np.median([t[k] for t in ts])) for k in range(5)]
+    step, ins = med[0], med[2]
+    nvox = nx * ny * nz
+    # the fill's bytes: 8 B (S, W) read + 4 B value + 1/8 B mask per voxel
+    tri_fill_bytes = nvox * (8 + 4) + nz * ny * ((nx + 31) // 32) * 4
     samples = w.n * w.H * w.W
     # distinct voxels the sweep's one insertion launch touches (W > 0 after
     # the last repetition's insert) and the insert's algorithmic bytes:
@@ -392,6 +397,11 @@ def measure_variants(dev, reps: int = 5, frames: int = 0, tune: bool = True):
                     f"{w.grid[0]}x{w.grid[1]}x{w.grid[2]} @ 0.4 mm",
         "ms_per_sweep": step, "frames_per_s": w.n / step * 1e3,
         "insert_ms": ins, "samples_per_s": samples / ins * 1e3, "tile": list(tri_tile),
+        "stage_ms": {"reset": med[1], "insert": med[2], "fill": med[3], "project": med[4]},
+        "fill_roofline": {"bound": "hbm", "algorithmic_bytes": tri_fill_bytes,
+                          "achieved": tri_fill_bytes / (med[3] / 1e3) / 1e9, "peak": peak,
+                          "unit": "GB/s",
+                          "frac": tri_fill_bytes / (med[3] / 1e3) / 1e9 / peak},
         "touched_voxels": touched,
         "roofline": {"bound": "hbm", "algorithmic_bytes": tri_bytes,
                      "achieved": tri_bytes / (ins / 1e3) / 1e9, "peak": peak, "unit": "GB/s",

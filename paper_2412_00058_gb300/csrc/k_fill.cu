@@ -456,6 +456,192 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
         atomicOr(a.status, USV_STATUS_SATURATED);
 }
 
+// ---- trilinear fill -----------------------------------------------------
+//
+// The nearest-neighbour fill's tiling and plane ring on (S, W) float pairs:
+// a 32 x 32 column tile marched along z by 32 x 8 threads (4 rows each),
+// one TMA tensor copy per plane two planes ahead into a 5-slot ring (zero
+// fill outside the grid), bounded mbarrier waits.  Per plane each thread
+// forms FP32 x-row sums of S and W for its 6 rows and from them the 3x3
+// plane sums of its 4 voxels; the 3x3x3 sums add three planes.  A voxel with
+// W > 0 takes S/W; an empty one (its own S and W are zero, so they add
+// nothing) the pooled sum of S over the pooled sum of W of its neighbours;
+// one IEEE division each.  One OR of each plane's W words skips the
+// arithmetic of planes without data.
+__global__ void __launch_bounds__(FTX *FBY, 4)
+    k_fill_tri(FillArgs a, const __grid_constant__ CUtensorMap map)
+{
+    constexpr int NT = FTX * FBY;
+    constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries per thread (OR pass)
+    constexpr int RS = kTmaW;                    // ring row stride (entries)
+    constexpr int CO = 1;                        // ring column of halo column 0
+    constexpr int SLOT = kTmaSlot;
+    extern __shared__ __align__(128) unsigned long long Pring[];  // [FSLOTS][FPY][RS]
+    __shared__ unsigned sflag[FSLOTS];
+    __shared__ __align__(8) unsigned long long sbar[FSLOTS];
+    __shared__ int s_abort;
+    auto *val = static_cast<float *>(a.val);
+    const int x0 = a.rx0 + blockIdx.x * FTX, y0 = a.ry0 + blockIdx.y * FTY;
+    const int z0 = a.rz0 + blockIdx.z * a.zchunk, z1 = min(a.rz1, z0 + a.zchunk);
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * FTX + tx;
+    const int x = x0 + tx, yb = 4 * ty;  // first of this thread's rows (tile-local)
+    const size_t plane = (size_t)a.nx * a.ny;
+    const unsigned sbase = (unsigned)__cvta_generic_to_shared(Pring);
+    const unsigned bbase = (unsigned)__cvta_generic_to_shared(sbar);
+    unsigned phase = 0u;    // parity of each slot's next completion
+    unsigned pending = 0u;  // thread 0: slots with a copy in flight
+
+    int soff[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int i = tid + k * NT;
+        const int ly = i / FPX, lx = i - ly * FPX;
+        soff[k] = ly * RS + lx + CO;
+    }
+    auto issue = [&](int pl) {
+        // (plane -1 is a real ring entry: the zero plane below the grid)
+        if (tid == 0 && pl <= z1) {
+            const int s = (pl + FSLOTS) % FSLOTS;
+            mbar_expect_tx(bbase + 8u * s, kTmaBytes);
+            tma_load_3d(sbase + (unsigned)(s * SLOT * 8), &map, x0 - 2, y0 - 1, pl,
+                        bbase + 8u * s);
+            pending |= 1u << s;
+        }
+    };
+    // TMA writes whole 128-byte-aligned slots; a ring that is not aligned is
+    // refused (reported as a failed wait) before any copy is issued
+    if ((sbase & 127u) != 0u) {
+        if (tid == 0)
+            atomicOr(a.status, USV_STATUS_TIMEOUT);
+        return;
+    }
+    if (tid < FSLOTS)
+        sflag[tid] = 0u;
+    if (tid == 0) {
+        s_abort = 0;
+        for (int s = 0; s < FSLOTS; ++s)
+            mbar_init(bbase + 8u * s, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    // 3x3 plane sums (S, W) of this thread's rows; plane p lives in slot p % 3
+    float2 B[3][FRW];
+    int nzf[3] = {0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int r = 0; r < FRW; ++r)
+            B[k][r] = make_float2(0.0f, 0.0f);
+
+    const bool xin = x < a.nx;
+    float *vout = val + ((size_t)z0 * a.ny + y0 + yb) * a.nx + x;
+    uint32_t *mout = a.mask + ((size_t)z0 * a.ny + y0 + yb) * a.nxw + (x0 >> 5);
+    const size_t mplane = (size_t)a.ny * a.nxw;
+    const int nrows = min(FRW, a.ny - (y0 + yb));  // rows of this thread inside the grid
+
+    // returns false when the CTA gives up (a wait ran out)
+    auto step = [&](int pl, int slot, float2(&Bn)[FRW], int &nzn) {
+        issue(pl + 2);
+        if (!mbar_wait(bbase + 8u * slot, (phase >> slot) & 1u)) {
+            s_abort = 1;
+            atomicOr(a.status, USV_STATUS_TIMEOUT);
+        }
+        phase ^= 1u << slot;
+        if (tid == 0)
+            pending &= ~(1u << slot);
+        const float2 *Pp = reinterpret_cast<const float2 *>(Pring + slot * SLOT);
+        unsigned orv = 0u;
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (tid + k * NT < FPLANE)
+                orv |= __float_as_uint(Pp[soff[k]].y);
+        orv = __reduce_or_sync(0xFFFFFFFFu, orv);
+        if (tx == 0 && orv)
+            atomicOr(&sflag[slot], orv);
+        __syncthreads();  // the plane has landed for every thread; flags complete
+        const unsigned fl = sflag[slot];
+        if (tid == 0)
+            sflag[slot == 0 ? FSLOTS - 1 : slot - 1] = 0u;  // read by everyone last step
+        nzn = fl != 0u;
+#pragma unroll
+        for (int r = 0; r < FRW; ++r)
+            Bn[r] = make_float2(0.0f, 0.0f);
+        if (nzn) {
+            float2 Rw[FRW + 2];
+#pragma unroll
+            for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 = halo rows yb .. yb+5
+                const float2 *row = Pp + (yb + k) * RS + tx + CO;
+                const float2 p0 = row[0], p1 = row[1], p2 = row[2];
+                Rw[k] = make_float2(p0.x + p1.x + p2.x, p0.y + p1.y + p2.y);
+            }
+#pragma unroll
+            for (int r = 0; r < FRW; ++r)
+                Bn[r] = make_float2(Rw[r].x + Rw[r + 1].x + Rw[r + 2].x,
+                                    Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
+        }
+        const int z = pl - 1;
+        if (z >= z0) {
+            const int sz = slot == 0 ? FSLOTS - 1 : slot - 1;  // plane z
+            const float2 *Pz = reinterpret_cast<const float2 *>(Pring + sz * SLOT);
+            const bool any = nzf[0] | nzf[1] | nzf[2];
+#pragma unroll
+            for (int r = 0; r < FRW; ++r) {
+                float v = 0.0f;
+                bool has = false;
+                if (any) {
+                    const float2 own = Pz[(yb + r + 1) * RS + tx + 1 + CO];
+                    const float S = own.y > 0.0f ? own.x : B[0][r].x + B[1][r].x + B[2][r].x;
+                    const float W = own.y > 0.0f ? own.y : B[0][r].y + B[1][r].y + B[2][r].y;
+                    has = W > 0.0f;
+                    if (has)
+                        v = __fdiv_rn(S, W);
+                }
+                const bool yin = r < nrows;
+                if (xin && yin &&
+                    guard((vout + (size_t)r * a.nx) - val, plane * a.nz, a.status))
+                    vout[(size_t)r * a.nx] = v;
+                const unsigned bits = __ballot_sync(0xFFFFFFFFu, xin && yin && has);
+                if (tx == 0 && yin &&
+                    guard((mout + (size_t)r * a.nxw) - a.mask,
+                          (size_t)a.nxw * a.ny * a.nz, a.status))
+                    mout[(size_t)r * a.nxw] = bits;
+            }
+            vout += plane;
+            mout += mplane;
+        }
+        __syncthreads();  // ring slot reuse
+        return !s_abort;
+    };
+
+    issue(z0 - 1);
+    issue(z0);
+    int slot = (z0 - 1 + FSLOTS) % FSLOTS;
+    bool ok = true;
+    // plane p's sums go to B[(p - z0 + 1) % 3]; unrolled by 3 so the slot is static
+    for (int pl = z0 - 1; pl <= z1 && ok; pl += 3) {
+        ok = step(pl, slot, B[0], nzf[0]);
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
+        if (!ok || pl + 1 > z1)
+            break;
+        ok = step(pl + 1, slot, B[1], nzf[1]);
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
+        if (!ok || pl + 2 > z1)
+            break;
+        ok = step(pl + 2, slot, B[2], nzf[2]);
+        slot = slot + 1 == FSLOTS ? 0 : slot + 1;
+    }
+    // after a timeout: wait (bounded) for the copies still in flight, so none
+    // lands in shared memory after the CTA has gone
+    if (tid == 0)
+        for (int s = 0; s < FSLOTS; ++s)
+            if (pending & (1u << s))
+                mbar_wait(bbase + 8u * s, (phase >> s) & 1u);
+}
+
+// Without TMA (odd nx): one thread per voxel, 32 x 8 tiles, three planes of
+// the tile and its halo in shared memory, the 27 neighbours summed in turn.
 __global__ void __launch_bounds__(TX *TY) k_fill_f32(FillArgs a)
 {
     __shared__ float2 pl[3][PY][PX];
@@ -604,6 +790,19 @@ cudaError_t launch_fill_pnn(const Volume &v, const int *lo, const int *hi, cudaS
 cudaError_t launch_fill_trilinear(const Volume &v, const int *lo, const int *hi, cudaStream_t st)
 {
     FillArgs a{v.acc, v.val, v.mask, v.status, v.g.nx, v.g.ny, v.g.nz, v.nxw, 0, 0, 0, 0, 0};
+    alignas(64) CUtensorMap map;
+    if (acc_tensor_map(v, v.acc, kTmaW, FPY, &map)) {
+        // ~6 waves of 4 resident CTAs per SM; slabs of at least 16 planes
+        const dim3 grid = fill_grid(a, FTX, FTY, 4 * 6, lo, hi, v.num_sms, 16);
+        if (grid.x == 0 || grid.y == 0 || grid.z == 0)
+            return cudaSuccess;
+        const int smem = FSLOTS * kTmaSlot * 8;
+        const cudaError_t e = prepare_kernel(reinterpret_cast<const void *>(k_fill_tri), smem);
+        if (e != cudaSuccess)
+            return e;
+        k_fill_tri<<<grid, dim3(FTX, FBY), smem, st>>>(a, map);
+        return cudaGetLastError();
+    }
     const dim3 grid = fill_grid(a, TX, TY, 8 * 8, lo, hi, v.num_sms, 16);
     if (grid.x == 0 || grid.y == 0 || grid.z == 0)
         return cudaSuccess;
