@@ -138,33 +138,52 @@ __device__ void patch_box(const TriArgs &a, const FrameRec *r, int j0, int j1, i
     }
 }
 
-// Corners of a cell that a step to a face-adjacent cell leaves behind: the
-// step moves by one along the axis of corner bit `abit`, up or down; moving
-// up, the corners with that bit clear stay behind (the others become the
-// new cell's corners with the bit clear), moving down the corners with the
-// bit set.  Any other step (or the end of a column) leaves all 8 behind.
-__device__ __forceinline__ bool left_behind(int c, bool face, int abit, bool up)
+// Corners of a cell that a step to a face-adjacent cell leaves behind, as
+// a bit mask over the 8 corners (bit c: corner c): the step moves by one
+// along the axis of corner bit `abit`, up or down; moving up, the corners
+// with that bit clear stay behind (the others become the new cell's corners
+// with the bit clear), moving down the corners with the bit set.  Any other
+// step (or the end of a column) leaves all 8 behind.
+__device__ __forceinline__ unsigned left_behind(bool face, int abit, bool up)
 {
-    return !face || (((c & abit) == 0) == up);
+    if (!face)
+        return 0xFFu;
+    const unsigned clear = abit == 1 ? 0x55u : abit == 2 ? 0x33u : 0x0Fu;
+    return up ? clear : 0xFFu & ~clear;
 }
 
-// Send a cell's corner terms to HBM, one vector atomic (S, W) per corner.
+// Send the corners in `send` of the cell at (lx, ly, lz) to HBM, one vector
+// atomic (S, W) per corner that holds a term.  The corner addresses are the
+// cell's base offset plus 0 or 1 entry, the row pitch and the plane pitch,
+// formed once per cell; in tiles the grid clips, corners outside it are
+// dropped by one mask per axis.
 template <bool CHECK>
 __device__ __forceinline__ void splat(float2 *acc, uint32_t *status, unsigned ex, unsigned ey,
                                       unsigned ez, int lx, int ly, int lz, const float (&cS)[8],
-                                      const float (&cW)[8], bool face = false, int abit = 1,
-                                      bool up = true)
+                                      const float (&cW)[8], unsigned send = 0xFFu)
 {
+    if (CHECK) {
+        const unsigned okx = ((unsigned)lx < ex ? 0x55u : 0u) | ((unsigned)(lx + 1) < ex ? 0xAAu : 0u);
+        const unsigned oky = ((unsigned)ly < ey ? 0x33u : 0u) | ((unsigned)(ly + 1) < ey ? 0xCCu : 0u);
+        const unsigned okz = ((unsigned)lz < ez ? 0x0Fu : 0u) | ((unsigned)(lz + 1) < ez ? 0xF0u : 0u);
+        send &= okx & oky & okz;
+    }
+    // entry offsets of corner 0 and of the +y, +z and +y+z corners (signed:
+    // in a clipped tile corner 0 itself may lie outside the grid)
+    const long long plane = (long long)ex * ey;
+    const long long i0 = ((long long)lz * ey + ly) * (long long)ex + lx;
+    const long long off[4] = {i0, i0 + ex, i0 + plane, i0 + plane + ex};
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const int cx = c & 1, cy = (c >> 1) & 1, cz = c >> 2;
-        if (cW[c] == 0.0f || !left_behind(c, face, abit, up))
-            continue;
-        const unsigned X = (unsigned)(lx + cx), Y = (unsigned)(ly + cy), Z = (unsigned)(lz + cz);
-        if (CHECK && !(X < ex && Y < ey && Z < ez))
-            continue;
-        const size_t i = ((size_t)Z * ey + Y) * ex + X;
-        if (guard(X, ex, status) && guard(Y, ey, status) && guard(Z, ez, status))
+        const long long i = off[c >> 1] + (c & 1);
+        const bool go = ((send >> c) & 1u) && cW[c] != 0.0f;
+        if constexpr (kChecked) {
+            const unsigned X = (unsigned)(lx + (c & 1)), Y = (unsigned)(ly + ((c >> 1) & 1)),
+                           Z = (unsigned)(lz + (c >> 2));
+            if (go && !(guard(X, ex, status) && guard(Y, ey, status) && guard(Z, ez, status)))
+                continue;
+        }
+        if (go)
             atomicAdd(acc + i, make_float2(cS[c], cW[c]));
     }
 }
@@ -235,8 +254,8 @@ __device__ __forceinline__ void walk(const TriArgs &a, const FrameRec *recs, int
                 const int abit = dx != 0 ? 1 : dy != 0 ? 2 : 4;
                 const bool up = dx + dy + dz > 0;
                 if (cx0 != INT_MIN)
-                    splat<CHECK>(a.acc, a.status, ex, ey, ez, cx0, cy0, cz0, cS, cW, face, abit,
-                                 up);
+                    splat<CHECK>(a.acc, a.status, ex, ey, ez, cx0, cy0, cz0, cS, cW,
+                                 left_behind(face, abit, up));
                 // new corner c is old corner c ^ abit when it receives: 0/1
                 // masks and multiply-adds (exact: one term is kept, the others
                 // are multiplied by zero) keep this off the integer pipe
