@@ -38,9 +38,15 @@
 //    two words (sum, count) -> two atomics; if the box does not fit in
 //    shared memory (pixels as coarse as voxels, steep poses) every pixel
 //    goes straight to an HBM atomic;
-//  * bounds checks run only in tiles whose box was clipped by the grid, and
-//    there once per segment: along a row every voxel index is monotone, so a
-//    segment whose two end pixels are inside the box is inside;
+//  * a tile that the grid clips keeps its whole (unclipped) box when that
+//    fits: its pixels outside the grid land in box entries outside the grid,
+//    which the flush drops, so every segment takes the checked-free inner
+//    loop (a segment cut by the grid would otherwise run a per-pixel checked
+//    loop, and with it every warp that holds one, beside the fast one);
+//  * only when the whole box does not fit is the box clipped to the grid;
+//    bounds checks then run once per segment: along a row every voxel index
+//    is monotone, so a segment whose two end pixels are inside the box is
+//    inside;
 //  * the flush takes the box 4 entries at a time (one 16-byte load), in row
 //    order, with exact multiply-high divisions for the row indices.
 #include <climits>
@@ -413,7 +419,7 @@ template <int TW, bool VEC>
 __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int group)
 {
     extern __shared__ __align__(16) unsigned box[];
-    __shared__ int s_lo[3], s_ext[3], s_zs, s_ex4, s_mode, s_check;
+    __shared__ int s_lo[3], s_ext[3], s_zs, s_ex4, s_mode, s_check, s_spill;
     __shared__ FrameRec s_rec[kMaxFpc];
     __shared__ long long s_q0[kMaxFpc][3];
 
@@ -453,25 +459,55 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
         const unsigned any = __reduce_or_sync(0xFFFFFFFFu, (unsigned)valid);
         const unsigned nsum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
         if (lane == 0) {
-            int mode = MODE_SKIP, check = 0, zs = 0, ex4 = 0;
+            int mode = MODE_SKIP, check = 0, zs = 0, ex4 = 0, spill = 0;
+            // box row stride: ex rounded up to 4; plane stride 4 mod 8
+            auto strides = [](const long long (&e)[3], int &r4, long long &z) {
+                r4 = (int)((e[0] + 3) & ~3LL);
+                z = (long long)r4 * e[1];
+                z += (z & 4) ? 0 : 4;
+                return z * e[2];
+            };
             if (any) {
                 const int n[3] = {a.nx, a.ny, a.nz};
                 mode = MODE_PACKED;
+                long long ce[3], ue[3];
+                int cl[3];
+                bool small = true;
                 for (int ax = 0; ax < 3; ++ax) {
                     const int l = max(lo[ax], 0), h = min(hi[ax], n[ax] - 1);
                     if (l > h)
                         mode = MODE_SKIP;
                     if (l != lo[ax] || h != hi[ax])
                         check = 1;
-                    s_lo[ax] = l;
-                    s_ext[ax] = max(h - l + 1, 0);
+                    cl[ax] = l;
+                    ce[ax] = max(h - l + 1, 0);
+                    ue[ax] = (long long)hi[ax] - lo[ax] + 1;
+                    small = small && ue[ax] <= kBoxWords;
                 }
-                if (mode != MODE_SKIP) {
-                    // row stride: ex rounded up to 4; plane stride 4 mod 8
-                    ex4 = (s_ext[0] + 3) & ~3;
-                    long long z = (long long)ex4 * s_ext[1];
-                    z += (z & 4) ? 0 : 4;
-                    const long long words = z * s_ext[2];
+                if (mode != MODE_SKIP && check && small && nsum <= kPackedMaxCount) {
+                    // a tile the grid clips takes its whole box if that fits:
+                    // every pixel then lands in the box with no bounds check,
+                    // and the flush drops the entries outside the grid
+                    int r4;
+                    long long z;
+                    if (strides(ue, r4, z) <= kBoxWords) {
+                        spill = 1;
+                        check = 0;
+                        ex4 = r4;
+                        zs = (int)z;
+                        for (int ax = 0; ax < 3; ++ax) {
+                            s_lo[ax] = lo[ax];
+                            s_ext[ax] = (int)ue[ax];
+                        }
+                    }
+                }
+                if (mode != MODE_SKIP && !spill) {
+                    for (int ax = 0; ax < 3; ++ax) {
+                        s_lo[ax] = cl[ax];
+                        s_ext[ax] = (int)ce[ax];
+                    }
+                    long long z;
+                    const long long words = strides(ce, ex4, z);
                     zs = (int)min(z, (long long)INT_MAX);
                     if (nsum <= kPackedMaxCount && words <= kBoxWords)
                         mode = MODE_PACKED;
@@ -483,6 +519,7 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
             }
             s_mode = mode;
             s_check = check;
+            s_spill = spill;
             s_zs = zs;
             s_ex4 = ex4;
         }
@@ -497,7 +534,7 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
         const int fi = threadIdx.x / 3, ax = threadIdx.x % 3;
         const FrameRec *r = s_rec + fi;
         const long long off =
-            (1LL << 31) - (mode == MODE_DIRECT ? 0LL : ((long long)s_lo[ax] << 32));
+            (1LL << 31) - (mode == MODE_DIRECT ? 0LL : (long long)s_lo[ax] * (1LL << 32));
         s_q0[fi][ax] =
             r->q[6 + ax] + (long long)u0 * r->q[ax] + (long long)v0 * r->q[3 + ax] + off;
     }
@@ -548,13 +585,16 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
     // row (y, z) = (row % ey, row / ey), both by exact multiply-high
     // division.  Each touched entry goes to HBM with one packed 64-bit
     // atomic; the x padding of a row is never touched, so it is skipped as
-    // empty.
+    // empty.  The whole box of a clipped tile (spill) may hold entries
+    // outside the grid: they are dropped here, by row and by entry.
     {
         const unsigned qr = bx.ex4 / 4, nq = qr * bx.ey * bx.ez;
         const unsigned mq = div_magic(qr), my = div_magic(bx.ey);
-        const size_t gplane = (size_t)a.nx * a.ny;
-        unsigned long long *gbase =
-            a.acc + ((size_t)s_lo[2] * a.ny + s_lo[1]) * a.nx + s_lo[0];
+        const long long gplane = (long long)a.nx * a.ny;
+        const bool spill = s_spill != 0;
+        // signed: a spilled box may start before the grid
+        const long long gbase = ((long long)s_lo[2] * a.ny + s_lo[1]) * a.nx + s_lo[0];
+        const unsigned long long nvox = (unsigned long long)a.nx * a.ny * a.nz;
         for (unsigned p = threadIdx.x; p < nq; p += kThreads) {
             const unsigned row = div_by(p, qr, mq), qx4 = 4u * (p - row * qr);
             const unsigned lz = div_by(row, bx.ey, my), ly = row - lz * bx.ey;
@@ -565,7 +605,18 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
                 c4 = *reinterpret_cast<const uint4 *>(box + cap + off);
             if ((e.x | e.y | e.z | e.w | c4.x | c4.y | c4.z | c4.w) == 0u)
                 continue;
-            unsigned long long *dst = gbase + lz * gplane + (size_t)ly * a.nx + qx4;
+            unsigned xin = 0xFu;  // entries of the quad inside the grid
+            if (spill) {
+                if ((unsigned)(s_lo[1] + (int)ly) >= (unsigned)a.ny ||
+                    (unsigned)(s_lo[2] + (int)lz) >= (unsigned)a.nz)
+                    continue;
+                const int gx = s_lo[0] + (int)qx4;
+                xin = 0u;
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    xin |= ((unsigned)(gx + k) < (unsigned)a.nx ? 1u : 0u) << k;
+            }
+            const long long gi = gbase + (long long)lz * gplane + (long long)ly * a.nx + qx4;
             const unsigned ev[4] = {e.x, e.y, e.z, e.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -577,9 +628,9 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
                     sv = ev[k];
                     cn = cv[k];
                 }
-                    if (cn != 0u && guard(qx4 + k, bx.ex, a.status) &&
-                    guard((dst + k) - a.acc, (unsigned long long)a.nx * a.ny * a.nz, a.status))
-                    atomicAdd(dst + k, pack64(sv, cn));
+                if (cn != 0u && ((xin >> k) & 1u) && guard(qx4 + k, bx.ex, a.status) &&
+                    guard((unsigned long long)(gi + k), nvox, a.status))
+                    atomicAdd(a.acc + (gi + k), pack64(sv, cn));
             }
         }
     }
