@@ -330,11 +330,14 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
                                          const long long (*q0)[3])
 {
     constexpr int S = TW / kSeg;                 // segments per tile row
+    // a tile cut by the frame's right edge has fewer segments per row: its
+    // items pack into fewer warps rather than leave lanes idle in every warp
+    const int Se = min(S, (u1 - u0 + kSeg - 1) / kSeg);
     const int nrows = v1 - v0;
     const int q = (nrows + 3) >> 2;              // rows per residue class mod 4
-    const int items = S * 4 * q;
+    const int items = Se * 4 * q;
     for (int it = threadIdx.x; it < items; it += kThreads) {
-        const int s = it % S, rp = it / S;
+        const int s = Se == S ? it % S : it % Se, rp = Se == S ? it / S : it / Se;
         const int r = 4 * (rp % q) + rp / q;     // consecutive lanes: rows 4 apart
         const int u = u0 + kSeg * s;
         if (r >= nrows || u >= u1)
