@@ -80,10 +80,14 @@ __device__ __forceinline__ void load_plane(T (*pl)[PX], const T *acc, int z, con
 // each thread forms the x-row sums of its 6 rows (y-1 .. y+4) and from them
 // the 3x3 plane sums of its 4 voxels (registers, kept for three planes);
 // the 3x3x3 sum is the sum of three plane sums, own voxel included (an
-// empty voxel adds zero).  One OR over each plane tells whether it is all
-// zero (then the tile writes zeros without arithmetic) and whether any
-// accumulator reaches 2^24 (then that output plane takes a direct 64-bit
-// path); below 2^24 every sum, and the mean's 2S + C, is exact in 32 bits.
+// empty voxel adds zero).  An OR of the words a thread sums tells whether
+// its window of the plane is all zero (then its voxels take no arithmetic)
+// and whether any count reaches 2^16 or any sum 2^24 (then its voxels of
+// that output plane take a direct 64-bit path); below those every sum, and
+// the mean's 2S + C, is exact in 32 bits.  With tensor copies each thread
+// waits for the plane on the mbarrier and decides alone, so the CTA meets
+// at one barrier per plane (slot reuse); with per-entry copies the flags
+// are the CTA's, after a second barrier.
 constexpr int FTX = 32, FTY = 32, FBY = 8, FRW = 4;  // FRW rows per thread
 constexpr int FPX = FTX + 2, FPY = FTY + 2, FPLANE = FPX * FPY;
 constexpr int FSLOTS = 5;
@@ -313,39 +317,68 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
             cp_async_wait<2>();
         }
         const unsigned long long *Pp = Pring + slot * SLOT;
-        unsigned orv = 0u;
-#pragma unroll
-        for (int k = 0; k < PER; ++k)
-            if (tid + k * NT < FPLANE) {
-                const unsigned long long w = Pp[soff[k]];
-                orv |= (unsigned)w | (unsigned)(w >> 32);
-            }
-        orv = __reduce_or_sync(0xFFFFFFFFu, orv);
-        if (tx == 0 && orv)
-            atomicOr(&sflag[slot], orv);
-        __syncthreads();  // the plane has landed for every thread; flags complete
-        const unsigned fl = sflag[slot];
-        if (tid == 0)
-            sflag[slot == 0 ? FSLOTS - 1 : slot - 1] = 0u;  // read by everyone last step
-        nzn = fl != 0u;
-        bign = fl >= kBig;
 #pragma unroll
         for (int r = 0; r < FRW; ++r)
             Bn[r] = make_uint2(0, 0);
-        if (nzn && !bign) {
-            uint2 Rw[FRW + 2];
+        if (TMA) {
+            // every thread has seen the copy complete on the mbarrier, so the
+            // plane is visible to it; the flags are this thread's own, over
+            // the 6 x 3 words it sums, which are all the words its 4 voxels'
+            // neighbourhoods in this plane read
+            // x-row sums of rows yb-1 .. yb+4 (halo rows yb .. yb+5), two
+            // kept at a time, each plane sum formed as soon as its 3 rows are in
+            uint2 R0 = make_uint2(0, 0), R1 = make_uint2(0, 0);
+            // OR of the packed words: a count at or above 2^16 or a sum at or
+            // above 2^24 takes the exact 64-bit path
+            unsigned long long orv = 0ull;
 #pragma unroll
-            for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 = halo rows yb .. yb+5
+            for (int k = 0; k < FRW + 2; ++k) {
                 const unsigned long long *row = Pp + (yb + k) * RS + tx + CO;
                 const unsigned long long p0 = row[0], p1 = row[1], p2 = row[2];
-                Rw[k] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
-                                   (unsigned)(p0 >> 32) + (unsigned)(p1 >> 32) +
-                                       (unsigned)(p2 >> 32));
+                const unsigned c0 = (unsigned)(p0 >> 32), c1 = (unsigned)(p1 >> 32),
+                               c2 = (unsigned)(p2 >> 32);
+                const unsigned s0 = (unsigned)p0, s1 = (unsigned)p1, s2 = (unsigned)p2;
+                orv |= p0 | p1 | p2;
+                const uint2 R2 = make_uint2(s0 + s1 + s2, c0 + c1 + c2);
+                if (k >= 2)
+                    Bn[k - 2] = make_uint2(R0.x + R1.x + R2.x, R0.y + R1.y + R2.y);
+                R0 = R1;
+                R1 = R2;
             }
+            nzn = orv != 0ull;
+            bign = (orv & 0xFFFF0000FF000000ull) != 0ull;
+        } else {
+            unsigned orv = 0u;
 #pragma unroll
-            for (int r = 0; r < FRW; ++r)
-                Bn[r] = make_uint2(Rw[r].x + Rw[r + 1].x + Rw[r + 2].x,
-                                   Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
+            for (int k = 0; k < PER; ++k)
+                if (tid + k * NT < FPLANE) {
+                    const unsigned long long w = Pp[soff[k]];
+                    orv |= (unsigned)w | (unsigned)(w >> 32);
+                }
+            orv = __reduce_or_sync(0xFFFFFFFFu, orv);
+            if (tx == 0 && orv)
+                atomicOr(&sflag[slot], orv);
+            __syncthreads();  // every thread's copies have landed; flags complete
+            const unsigned fl = sflag[slot];
+            if (tid == 0)
+                sflag[slot == 0 ? FSLOTS - 1 : slot - 1] = 0u;  // read by everyone last step
+            nzn = fl != 0u;
+            bign = fl >= kBig;
+            if (nzn && !bign) {
+                uint2 Rw[FRW + 2];
+#pragma unroll
+                for (int k = 0; k < FRW + 2; ++k) {
+                    const unsigned long long *row = Pp + (yb + k) * RS + tx + CO;
+                    const unsigned long long p0 = row[0], p1 = row[1], p2 = row[2];
+                    Rw[k] = make_uint2((unsigned)p0 + (unsigned)p1 + (unsigned)p2,
+                                       (unsigned)(p0 >> 32) + (unsigned)(p1 >> 32) +
+                                           (unsigned)(p2 >> 32));
+                }
+#pragma unroll
+                for (int r = 0; r < FRW; ++r)
+                    Bn[r] = make_uint2(Rw[r].x + Rw[r + 1].x + Rw[r + 2].x,
+                                       Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
+            }
         }
         const int z = pl - 1;
         if (z >= z0 && a.clear) {
