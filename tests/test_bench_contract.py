@@ -87,6 +87,10 @@ def test_gpu_arm_line():
     assert e["value"] > 0 and e["h2d_bytes_per_step"] == 600 * 640 * 480 + 600 * 128
     assert e["d2h_bytes_per_step"] > 0
     assert e["host_link"]["h2d_gbs"] > 0 and 0 < e["host_link"]["frac"] < 1.5
+    hl = e["host_link"]
+    assert hl["h2d_gbs"] == max(hl["h2d_gbs_before"], hl["h2d_gbs_after"])
+    assert len(e["runs_ms_per_step"]) == 3
+    assert e["ms_per_step"] == sorted(e["runs_ms_per_step"])[1]
     pr = d["pipeline_roofline"]
     assert pr["clear_bytes_per_step"] > 0 and 0 < pr["frac"] < 2
     assert set(d["stage_ms"]) == {"insert", "fill", "project", "gaps"}
