@@ -499,18 +499,16 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
 // plane sums of its 4 voxels; the 3x3x3 sums add three planes.  A voxel with
 // W > 0 takes S/W; an empty one (its own S and W are zero, so they add
 // nothing) the pooled sum of S over the pooled sum of W of its neighbours;
-// one IEEE division each.  One OR of each plane's W words skips the
-// arithmetic of planes without data.
+// one IEEE division each.  Each thread waits for the plane on the
+// mbarrier and needs no flag (the sums of a window without data are zero),
+// so the CTA meets at one barrier per plane, for slot reuse.
 __global__ void __launch_bounds__(FTX *FBY, 4)
     k_fill_tri(FillArgs a, const __grid_constant__ CUtensorMap map)
 {
-    constexpr int NT = FTX * FBY;
-    constexpr int PER = (FPLANE + NT - 1) / NT;  // plane entries per thread (OR pass)
     constexpr int RS = kTmaW;                    // ring row stride (entries)
     constexpr int CO = 1;                        // ring column of halo column 0
     constexpr int SLOT = kTmaSlot;
     extern __shared__ __align__(128) unsigned long long Pring[];  // [FSLOTS][FPY][RS]
-    __shared__ unsigned sflag[FSLOTS];
     __shared__ __align__(8) unsigned long long sbar[FSLOTS];
     __shared__ int s_abort;
     auto *val = static_cast<float *>(a.val);
@@ -524,13 +522,6 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
     unsigned phase = 0u;    // parity of each slot's next completion
     unsigned pending = 0u;  // thread 0: slots with a copy in flight
 
-    int soff[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int i = tid + k * NT;
-        const int ly = i / FPX, lx = i - ly * FPX;
-        soff[k] = ly * RS + lx + CO;
-    }
     auto issue = [&](int pl) {
         // (plane -1 is a real ring entry: the zero plane below the grid)
         if (tid == 0 && pl <= z1) {
@@ -548,8 +539,6 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
             atomicOr(a.status, USV_STATUS_TIMEOUT);
         return;
     }
-    if (tid < FSLOTS)
-        sflag[tid] = 0u;
     if (tid == 0) {
         s_abort = 0;
         for (int s = 0; s < FSLOTS; ++s)
@@ -561,7 +550,6 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
 
     // 3x3 plane sums (S, W) of this thread's rows; plane p lives in slot p % 3
     float2 B[3][FRW];
-    int nzf[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -575,7 +563,7 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
     const int nrows = min(FRW, a.ny - (y0 + yb));  // rows of this thread inside the grid
 
     // returns false when the CTA gives up (a wait ran out)
-    auto step = [&](int pl, int slot, float2(&Bn)[FRW], int &nzn) {
+    auto step = [&](int pl, int slot, float2(&Bn)[FRW]) {
         issue(pl + 2);
         if (!mbar_wait(bbase + 8u * slot, (phase >> slot) & 1u)) {
             s_abort = 1;
@@ -584,46 +572,30 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
         phase ^= 1u << slot;
         if (tid == 0)
             pending &= ~(1u << slot);
+        // every thread has seen the copy complete on the mbarrier, so the
+        // plane is visible to it; the sums of a window without data are
+        // zero, so no flag is needed
         const float2 *Pp = reinterpret_cast<const float2 *>(Pring + slot * SLOT);
-        unsigned orv = 0u;
+        float2 R0 = make_float2(0.0f, 0.0f), R1 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int k = 0; k < PER; ++k)
-            if (tid + k * NT < FPLANE)
-                orv |= __float_as_uint(Pp[soff[k]].y);
-        orv = __reduce_or_sync(0xFFFFFFFFu, orv);
-        if (tx == 0 && orv)
-            atomicOr(&sflag[slot], orv);
-        __syncthreads();  // the plane has landed for every thread; flags complete
-        const unsigned fl = sflag[slot];
-        if (tid == 0)
-            sflag[slot == 0 ? FSLOTS - 1 : slot - 1] = 0u;  // read by everyone last step
-        nzn = fl != 0u;
-#pragma unroll
-        for (int r = 0; r < FRW; ++r)
-            Bn[r] = make_float2(0.0f, 0.0f);
-        if (nzn) {
-            float2 Rw[FRW + 2];
-#pragma unroll
-            for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 = halo rows yb .. yb+5
-                const float2 *row = Pp + (yb + k) * RS + tx + CO;
-                const float2 p0 = row[0], p1 = row[1], p2 = row[2];
-                Rw[k] = make_float2(p0.x + p1.x + p2.x, p0.y + p1.y + p2.y);
-            }
-#pragma unroll
-            for (int r = 0; r < FRW; ++r)
-                Bn[r] = make_float2(Rw[r].x + Rw[r + 1].x + Rw[r + 2].x,
-                                    Rw[r].y + Rw[r + 1].y + Rw[r + 2].y);
+        for (int k = 0; k < FRW + 2; ++k) {  // rows yb-1 .. yb+4 = halo rows yb .. yb+5
+            const float2 *row = Pp + (yb + k) * RS + tx + CO;
+            const float2 p0 = row[0], p1 = row[1], p2 = row[2];
+            const float2 R2 = make_float2(p0.x + p1.x + p2.x, p0.y + p1.y + p2.y);
+            if (k >= 2)
+                Bn[k - 2] = make_float2(R0.x + R1.x + R2.x, R0.y + R1.y + R2.y);
+            R0 = R1;
+            R1 = R2;
         }
         const int z = pl - 1;
         if (z >= z0) {
             const int sz = slot == 0 ? FSLOTS - 1 : slot - 1;  // plane z
             const float2 *Pz = reinterpret_cast<const float2 *>(Pring + sz * SLOT);
-            const bool any = nzf[0] | nzf[1] | nzf[2];
 #pragma unroll
             for (int r = 0; r < FRW; ++r) {
                 float v = 0.0f;
                 bool has = false;
-                if (any) {
+                {
                     const float2 own = Pz[(yb + r + 1) * RS + tx + 1 + CO];
                     const float S = own.y > 0.0f ? own.x : B[0][r].x + B[1][r].x + B[2][r].x;
                     const float W = own.y > 0.0f ? own.y : B[0][r].y + B[1][r].y + B[2][r].y;
@@ -654,15 +626,15 @@ __global__ void __launch_bounds__(FTX *FBY, 4)
     bool ok = true;
     // plane p's sums go to B[(p - z0 + 1) % 3]; unrolled by 3 so the slot is static
     for (int pl = z0 - 1; pl <= z1 && ok; pl += 3) {
-        ok = step(pl, slot, B[0], nzf[0]);
+        ok = step(pl, slot, B[0]);
         slot = slot + 1 == FSLOTS ? 0 : slot + 1;
         if (!ok || pl + 1 > z1)
             break;
-        ok = step(pl + 1, slot, B[1], nzf[1]);
+        ok = step(pl + 1, slot, B[1]);
         slot = slot + 1 == FSLOTS ? 0 : slot + 1;
         if (!ok || pl + 2 > z1)
             break;
-        ok = step(pl + 2, slot, B[2], nzf[2]);
+        ok = step(pl + 2, slot, B[2]);
         slot = slot + 1 == FSLOTS ? 0 : slot + 1;
     }
     // after a timeout: wait (bounded) for the copies still in flight, so none
