@@ -62,6 +62,7 @@ constexpr int kSeg = 32;             // pixels per lane segment (two 16-byte loa
 constexpr int kSmem = 52 * 1024;     // dynamic shared memory per CTA (the box)
 constexpr int kBoxWords = kSmem / 4;
 constexpr int kMaxFpc = 8;           // frames per CTA (warp 0 takes 4 corners x 8 frames)
+constexpr int kMaxSeg = 256 / 32;    // segments per tile row, at most
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
 constexpr int kPackedMaxCount = 1023;
 
@@ -327,7 +328,8 @@ template <int TW, bool VEC, bool CHECK, int MODE>
 __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u0, int u1,
                                          int v0, int v1, const Box &bx, unsigned *box,
                                          unsigned cap, const FrameRec *recs,
-                                         const long long (*q0)[3])
+                                         const long long (*q0)[kMaxSeg][3],
+                                         const unsigned char *narrowf)
 {
     constexpr int S = TW / kSeg;                 // segments per tile row
     // a tile cut by the frame's right edge has fewer segments per row: its
@@ -344,7 +346,6 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
             continue;
         const int v = v0 + r;
         const int npx = VEC ? (u1 - u >= kSeg ? kSeg : 16) : min(kSeg, u1 - u);
-        const unsigned du = kSeg * s;
         const uint8_t *row = a.img + (size_t)v * a.W + u;
         const size_t fstride = (size_t)a.H * a.W;
         // the frames of the group whose row v is inserted (valid, below the cut)
@@ -365,9 +366,9 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
                 load_segment<VEC>(row + (size_t)(f0 + fn) * fstride, npx, n0, n1);
             const FrameRec *rr = recs + f;
             const long long Ax = rr->q[0], Ay = rr->q[1], Az = rr->q[2];
-            const long long qx = mad64((unsigned)r, rr->q[3], mad64(du, Ax, q0[f][0]));
-            const long long qy = mad64((unsigned)r, rr->q[4], mad64(du, Ay, q0[f][1]));
-            const long long qz = mad64((unsigned)r, rr->q[5], mad64(du, Az, q0[f][2]));
+            const long long qx = mad64((unsigned)r, rr->q[3], q0[f][s][0]);
+            const long long qy = mad64((unsigned)r, rr->q[4], q0[f][s][1]);
+            const long long qz = mad64((unsigned)r, rr->q[5], q0[f][s][2]);
             bool inside = true;
             if (CHECK) {
                 const long long e = npx - 1;
@@ -379,8 +380,7 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
                 long long x = qx, y = qy, z = qz;
                 const unsigned sbase = (unsigned)__cvta_generic_to_shared(box);
                 // steps below half a voxel: the wide multiply-add form
-                const bool narrow = Ax > -(1LL << 31) && Ax < (1LL << 31) &&
-                                    Az > -(1LL << 31) && Az < (1LL << 31);
+                const bool narrow = narrowf[f] != 0;
                 // the segment stays in one y layer (and so, by the vote, does
                 // every lane of the warp here): two coordinates per pixel
                 const bool yc = hi32(qy) == hi32(qy + (long long)(npx - 1) * Ay);
@@ -424,7 +424,8 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
     extern __shared__ __align__(16) unsigned box[];
     __shared__ int s_lo[3], s_ext[3], s_zs, s_ex4, s_mode, s_check, s_spill;
     __shared__ FrameRec s_rec[kMaxFpc];
-    __shared__ long long s_q0[kMaxFpc][3];
+    __shared__ long long s_q0[kMaxFpc][kMaxSeg][3];
+    __shared__ unsigned char s_narrow[kMaxFpc];
 
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int u0 = tx * TW, v0 = ty * a.th;
@@ -533,13 +534,21 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
         return;
     // each frame's Q at the tile corner (u0, v0), box-local (or global for
     // MODE_DIRECT), with the 2^31 of the rounding folded in
-    if (threadIdx.x < 3 * (f1 - f0)) {
-        const int fi = threadIdx.x / 3, ax = threadIdx.x % 3;
+    // and at each segment's first column (u0 + 32 s); per frame whether the
+    // x and z steps are below half a voxel (the wide multiply-add loop)
+    constexpr int S = TW / kSeg;
+    for (int i = threadIdx.x; i < 3 * S * (f1 - f0); i += kThreads) {
+        const int fi = i / (3 * S), sg = (i / 3) % S, ax = i % 3;
         const FrameRec *r = s_rec + fi;
         const long long off =
             (1LL << 31) - (mode == MODE_DIRECT ? 0LL : (long long)s_lo[ax] * (1LL << 32));
-        s_q0[fi][ax] =
-            r->q[6 + ax] + (long long)u0 * r->q[ax] + (long long)v0 * r->q[3 + ax] + off;
+        s_q0[fi][sg][ax] = r->q[6 + ax] + (long long)(u0 + kSeg * sg) * r->q[ax] +
+                           (long long)v0 * r->q[3 + ax] + off;
+    }
+    if (threadIdx.x < f1 - f0) {
+        const long long Ax = s_rec[threadIdx.x].q[0], Az = s_rec[threadIdx.x].q[2];
+        s_narrow[threadIdx.x] = Ax > -(1LL << 31) && Ax < (1LL << 31) &&
+                                Az > -(1LL << 31) && Az < (1LL << 31);
     }
     if (mode == MODE_DIRECT) {
         __syncthreads();
@@ -548,7 +557,7 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
                        (unsigned)a.nx * (unsigned)a.ny, (unsigned)a.nx,
                        (unsigned long long)a.nx * a.ny * a.nz, a.status};
         run_tile<TW, VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, g, nullptr, 0, s_rec,
-                                             s_q0);
+                                             s_q0, s_narrow);
         return;
     }
     const Box bx = {(unsigned)s_ext[0], (unsigned)s_ext[1], (unsigned)s_ext[2], (unsigned)s_zs,
@@ -570,17 +579,17 @@ __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int grou
     if (mode == MODE_PACKED) {
         if (s_check)
             run_tile<TW, VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, bx, box, 0, s_rec,
-                                                 s_q0);
+                                                 s_q0, s_narrow);
         else
             run_tile<TW, VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, bx, box, 0, s_rec,
-                                                  s_q0);
+                                                  s_q0, s_narrow);
     } else {
         if (s_check)
             run_tile<TW, VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, bx, box, cap, s_rec,
-                                                s_q0);
+                                                s_q0, s_narrow);
         else
             run_tile<TW, VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, bx, box, cap, s_rec,
-                                                 s_q0);
+                                                 s_q0, s_narrow);
     }
     __syncthreads();
     // Flush: the threads take the box's quads (4 consecutive x entries of one
