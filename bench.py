@@ -582,8 +582,8 @@ def run_gpu(args):
     if not args.no_tune:
         t_t0 = time.perf_counter()
         tile, tile_ms = vol.tune(imgs, poses, cal, stream)
-        tune = {"tile": list(tile), "default": [128, 64, 8],
-                "insert_ms_first_1024_frames": tile_ms, "candidates": 45,
+        tune = {"tile": list(tile), "default": [128, 64, 12],
+                "insert_ms_tuning_frames": tile_ms, "tuning_frames": min(w.n, 4096), "candidates": 50,
                 "seconds": time.perf_counter() - t_t0}
     vol.reset(stream)
     for _ in range(max(args.warmup, 3)):

@@ -87,7 +87,8 @@ typedef struct {
  * frames_per_cta consecutive frames (no counterpart in the paper; the
  * results do not depend on it, except for the FP32 summation order of the
  * trilinear mode).  USV_PNN: tile_w 64, 128 or 256, tile_h 1..1024,
- * frames_per_cta 1..8; default 128 x 64 x 8.  USV_TRILINEAR: tile_w 256,
+ * frames_per_cta 1..16 (1..8 with tile_w 256); default 128 x 64 x 12.
+ * USV_TRILINEAR: tile_w 256,
  * tile_h 1..128, frames_per_cta 1..8; default 256 x 64 x 4.  In USV_PNN,
  * frames_per_cta is an upper bound: a batch of frames too small to fill
  * the GPU is spread over more thread blocks with fewer frames each. */
@@ -320,12 +321,13 @@ int usv_insert_frames_multi(const usv_insert_job *jobs, int32_t njobs, void *str
 /* ------------------------------------------------------------------------
  * Tile shapes per frame size (no counterpart in the paper).
  * usv_tune_insert -- the insertion autotuner: inserts the first
- * min(n, 1024) of the given frames with each candidate tile shape into the
+ * min(n, 4096) of the given frames with each candidate tile shape into the
  * caller's scratch accumulators, times the insertion with CUDA events on
  * `stream` (the call waits for the stream), and keeps the fastest shape in
  * the volume for frames of H x W.  The volume's own accumulators are not
  * touched (its per-frame set-up scratch is).  Candidates: USV_PNN tile_w
- * {64, 128, 256} x tile_h {32, 48, 64, 96, 128} x frames_per_cta {4, 6, 8};
+ * {64, 128, 256} x tile_h {32, 48, 64, 96, 128} x frames_per_cta {4, 8, 12, 16}
+ * (at most 8 with tile_w 256);
  * USV_TRILINEAR tile_h {16, 32, 64, 128} x frames_per_cta {2, 4, 8}.
  *   scratch_dev    device, 16-byte aligned, >= 8 * nx * ny * nz bytes
  *   best_out       the chosen shape (may be NULL)

@@ -7,8 +7,12 @@
 //
 // GB300 design:
 //  * one CTA = a tile of TW columns x TH rows of FPC consecutive frames
-//    (default 128 x 64 x 8; TW is 64, 128 or 256, the shape is set per frame
-//    size or chosen by the autotuner).  A row of the tile is cut into
+//    (default 128 x 64 x 12; TW is 64, 128 or 256, FPC up to 16, 8 with
+//    TW 256; the shape is set per frame size or chosen by the autotuner).
+//    More frames per box means fewer flushes of each voxel and less set-up
+//    per pixel; a group of more than 8 frames whose box is too large for
+//    packed entries is done as two passes (its first 8 frames, then the
+//    rest), each with its own box.  A row of the tile is cut into
 //    segments of 32 pixels, each read by one lane with two coalesced 16-byte
 //    loads (a whole 32-byte sector); the next wanted frame's segment is
 //    loaded while this one is inserted;
@@ -48,8 +52,10 @@
 //    is monotone, so a segment whose two end pixels are inside the box is
 //    inside;
 //  * the flush takes the box 4 entries at a time (one 16-byte load), in row
-//    order, with exact multiply-high divisions for the row indices.
+//    order, with exact multiply-high divisions for the row indices; it is
+//    compiled per box mode, so its loop holds no mode tests.
 #include <climits>
+#include <cstddef>
 
 #include "usv_internal.cuh"
 
@@ -61,8 +67,8 @@ constexpr int kThreads = 256;
 constexpr int kSeg = 32;             // pixels per lane segment (two 16-byte loads)
 constexpr int kSmem = 52 * 1024;     // dynamic shared memory per CTA (the box)
 constexpr int kBoxWords = kSmem / 4;
-constexpr int kMaxFpc = 8;           // frames per CTA (warp 0 takes 4 corners x 8 frames)
-constexpr int kMaxSeg = 256 / 32;    // segments per tile row, at most
+constexpr int kMaxFpc = 16;          // frames per CTA (8 with 256-column tiles)
+constexpr int kHalfFpc = 8;          // warp 0 takes 4 corners x 8 frames, twice
 constexpr int kCountShift = 22;      // packed entry: count << 22 | sum
 constexpr int kPackedMaxCount = 1023;
 
@@ -78,6 +84,20 @@ struct PnnArgs {
     int th;                 // rows per tile
     int tiles_x;            // tiles per frame along u
     int fpc;                // frames per CTA
+};
+
+// The part of a frame record the insertion reads (its map and flags),
+// copied into shared memory.
+struct PnnRec {
+    long long q[9];
+    int valid, nmax, first_row, pad;
+};
+static_assert(offsetof(FrameRec, valid) == 144 && sizeof(PnnRec) == 88, "record layout");
+
+// How a CTA accumulates one pass over frames [fa, fb) of its group: box
+// origin and extents, strides, mode, checks.
+struct Plan {
+    int lo[3], ext[3], zs, ex4, mode, check, spill, fa, fb;
 };
 
 __device__ __forceinline__ unsigned hi32(long long q) { return (unsigned)(q >> 32); }
@@ -325,10 +345,10 @@ __device__ __forceinline__ void load_segment(const uint8_t *p, int npx, uint4 &w
 
 // All of the CTA's segments of all its frames, in one box mode.
 template <int TW, bool VEC, bool CHECK, int MODE>
-__device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u0, int u1,
+__device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int ga, int gb, int u0, int u1,
                                          int v0, int v1, const Box &bx, unsigned *box,
-                                         unsigned cap, const FrameRec *recs,
-                                         const long long (*q0)[kMaxSeg][3],
+                                         unsigned cap, const PnnRec *recs,
+                                         const long long (*q0)[TW / kSeg][3],
                                          const unsigned char *narrowf)
 {
     constexpr int S = TW / kSeg;                 // segments per tile row
@@ -350,7 +370,7 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
         const size_t fstride = (size_t)a.H * a.W;
         // the frames of the group whose row v is inserted (valid, below the cut)
         unsigned want = 0u;
-        for (int g = 0; g < f1 - f0; ++g)
+        for (int g = ga; g < gb; ++g)
             want |= (recs[g].valid && v >= recs[g].first_row ? 1u : 0u) << g;
         if (!want)
             continue;
@@ -364,7 +384,7 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
             uint4 n0 = make_uint4(0, 0, 0, 0), n1 = n0;
             if (fn >= 0)
                 load_segment<VEC>(row + (size_t)(f0 + fn) * fstride, npx, n0, n1);
-            const FrameRec *rr = recs + f;
+            const PnnRec *rr = recs + f;
             const long long Ax = rr->q[0], Ay = rr->q[1], Az = rr->q[2];
             const long long qx = mad64((unsigned)r, rr->q[3], q0[f][s][0]);
             const long long qy = mad64((unsigned)r, rr->q[4], q0[f][s][1]);
@@ -415,236 +435,313 @@ __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int f1, int u
     }
 }
 
+// The flush of a CTA's box: quad p is row p / qr, quad p % qr of it, the
+// row (y, z) = (row % ey, row / ey), both by exact multiply-high division.
+// The x padding of a row is never touched, so it is skipped as empty.  The
+// whole box of a clipped tile (SPILL) may hold entries outside the grid:
+// they are dropped here, by row and by entry.
+template <int MODE, bool SPILL>
+__device__ __forceinline__ void flush_box(const PnnArgs &a, const unsigned *box, unsigned cap,
+                                          const Box &bx, const int *lo)
+{
+    const unsigned qr = bx.ex4 / 4, nq = qr * bx.ey * bx.ez;
+    const unsigned mq = div_magic(qr), my = div_magic(bx.ey);
+    const long long gplane = (long long)a.nx * a.ny;
+    // signed: a spilled box may start before the grid
+    const long long gbase = ((long long)lo[2] * a.ny + lo[1]) * a.nx + lo[0];
+    const unsigned long long nvox = (unsigned long long)a.nx * a.ny * a.nz;
+#ifdef USV_FL32
+    // the box's span in the grid, in entries, fits 32 bits: offsets from the
+    // box's first entry are 32-bit
+    const bool n32 = (unsigned long long)bx.ez * (unsigned long long)gplane < (1ull << 32);
+    const unsigned gp32 = (unsigned)gplane, nx32 = (unsigned)a.nx;
+    unsigned long long *const gb = a.acc + gbase;
+#endif
+    for (unsigned p = threadIdx.x; p < nq; p += kThreads) {
+        const unsigned row = div_by(p, qr, mq), qx4 = 4u * (p - row * qr);
+        const unsigned lz = div_by(row, bx.ey, my), ly = row - lz * bx.ey;
+        const unsigned off = lz * bx.zs + ly * bx.ex4 + qx4;
+        const uint4 e = *reinterpret_cast<const uint4 *>(box + off);
+        uint4 c4 = e;
+        unsigned any = e.x | e.y | e.z | e.w;
+        if (MODE == MODE_SPLIT) {
+            c4 = *reinterpret_cast<const uint4 *>(box + cap + off);
+            any |= c4.x | c4.y | c4.z | c4.w;
+        }
+        if (any == 0u)
+            continue;
+        unsigned xin = 0xFu;  // entries of the quad inside the grid
+        if (SPILL) {
+            if ((unsigned)(lo[1] + (int)ly) >= (unsigned)a.ny ||
+                (unsigned)(lo[2] + (int)lz) >= (unsigned)a.nz)
+                continue;
+            const int gx = lo[0] + (int)qx4;
+            xin = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                xin |= ((unsigned)(gx + k) < (unsigned)a.nx ? 1u : 0u) << k;
+        }
+        const long long gi = gbase + (long long)lz * gplane + (long long)ly * a.nx + qx4;
+        unsigned long long *g = a.acc + gi;
+#ifdef USV_FL32
+        if (!kChecked && n32)
+            g = gb + (lz * gp32 + ly * nx32 + qx4);
+#endif
+        const unsigned ev[4] = {e.x, e.y, e.z, e.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned sv = MODE == MODE_PACKED ? ev[k] & ((1u << kCountShift) - 1) : ev[k];
+            const unsigned cn = MODE == MODE_PACKED ? ev[k] >> kCountShift : cv[k];
+            if (cn != 0u && (!SPILL || ((xin >> k) & 1u)) && guard(qx4 + k, bx.ex, a.status) &&
+                guard((unsigned long long)(gi + k), nvox, a.status))
+                atomicAdd(g + k, pack64(sv, cn));
+        }
+    }
+}
+
+// The box plan of a frame range from its voxel bounding box (lo, hi), its
+// validity and its bound on pixels per voxel (lane 0 of warp 0).
+__device__ __forceinline__ void plan_box(const PnnArgs &a, const int (&lo)[3], const int (&hi)[3],
+                                         bool any, unsigned nsum, Plan &p)
+{
+    // box row stride: ex rounded up to 4; plane stride 4 mod 8
+    auto strides = [](const long long (&e)[3], int &r4, long long &z) {
+        r4 = (int)((e[0] + 3) & ~3LL);
+        z = (long long)r4 * e[1];
+        z += (z & 4) ? 0 : 4;
+        return z * e[2];
+    };
+    int mode = MODE_SKIP, check = 0, zs = 0, ex4 = 0, spill = 0;
+    if (any) {
+        const int n[3] = {a.nx, a.ny, a.nz};
+        mode = MODE_PACKED;
+        long long ce[3], ue[3];
+        int cl[3];
+        bool small = true;
+        for (int ax = 0; ax < 3; ++ax) {
+            const int l = max(lo[ax], 0), h = min(hi[ax], n[ax] - 1);
+            if (l > h)
+                mode = MODE_SKIP;
+            if (l != lo[ax] || h != hi[ax])
+                check = 1;
+            cl[ax] = l;
+            ce[ax] = max(h - l + 1, 0);
+            ue[ax] = (long long)hi[ax] - lo[ax] + 1;
+            small = small && ue[ax] <= kBoxWords;
+        }
+        if (mode != MODE_SKIP && check && small && nsum <= kPackedMaxCount) {
+            // a tile the grid clips takes its whole box if that fits: every
+            // pixel then lands in the box with no bounds check, and the
+            // flush drops the entries outside the grid
+            int r4;
+            long long z;
+            if (strides(ue, r4, z) <= kBoxWords) {
+                spill = 1;
+                check = 0;
+                ex4 = r4;
+                zs = (int)z;
+                for (int ax = 0; ax < 3; ++ax) {
+                    p.lo[ax] = lo[ax];
+                    p.ext[ax] = (int)ue[ax];
+                }
+            }
+        }
+        if (mode != MODE_SKIP && !spill) {
+            for (int ax = 0; ax < 3; ++ax) {
+                p.lo[ax] = cl[ax];
+                p.ext[ax] = (int)ce[ax];
+            }
+            long long z;
+            const long long words = strides(ce, ex4, z);
+            zs = (int)min(z, (long long)INT_MAX);
+            if (nsum <= kPackedMaxCount && words <= kBoxWords)
+                mode = MODE_PACKED;
+            else if (words <= kBoxWords / 2)
+                mode = MODE_SPLIT;
+            else
+                mode = MODE_DIRECT;
+        }
+    }
+    p.mode = mode;
+    p.check = check;
+    p.spill = spill;
+    p.zs = zs;
+    p.ex4 = ex4;
+}
+
 // One CTA's work: tile `tile` of the frame group `group` (frames
 // group*fpc ..).  Every thread of the CTA calls it with the same arguments;
-// it leaves shared memory to be reused only after a barrier.
+// it leaves shared memory to be reused only after a barrier.  A group of
+// more than 8 frames whose box does not take the packed one-word entries in
+// shared memory is done as two passes of its first 8 and its other frames,
+// each with its own box.
 template <int TW, bool VEC>
 __device__ __forceinline__ void insert_tile(const PnnArgs &a, int tile, int group)
 {
+    constexpr int S = TW / kSeg;
+    constexpr int FPC = TW >= 256 ? kHalfFpc : kMaxFpc;
     extern __shared__ __align__(16) unsigned box[];
-    __shared__ int s_lo[3], s_ext[3], s_zs, s_ex4, s_mode, s_check, s_spill;
-    __shared__ FrameRec s_rec[kMaxFpc];
-    __shared__ long long s_q0[kMaxFpc][kMaxSeg][3];
-    __shared__ unsigned char s_narrow[kMaxFpc];
+    __shared__ Plan s_plan[2];
+    __shared__ int s_npass;
+    __shared__ PnnRec s_rec[FPC];
+    __shared__ long long s_q0[FPC][S][3];
+    __shared__ unsigned char s_narrow[FPC];
 
     const int tx = tile % a.tiles_x, ty = tile / a.tiles_x;
     const int u0 = tx * TW, v0 = ty * a.th;
     const int u1 = min(a.W, u0 + TW), v1 = min(a.H, v0 + a.th);
     const int f0 = group * a.fpc, f1 = min(a.n, f0 + a.fpc);
+    const int nf = f1 - f0;
 
-    // the CTA's frame records, copied once into shared memory
-    for (int i = threadIdx.x; i < (f1 - f0) * (int)(sizeof(FrameRec) / 8); i += kThreads)
-        reinterpret_cast<unsigned long long *>(s_rec)[i] =
-            reinterpret_cast<const unsigned long long *>(a.rec + f0)[i];
+    // the CTA's frame records (map and flags), copied once into shared memory
+    for (int i = threadIdx.x; i < nf * 11; i += kThreads) {
+        const int f = i / 11, w = i - 11 * f;
+        reinterpret_cast<unsigned long long *>(s_rec + f)[w] =
+            reinterpret_cast<const unsigned long long *>(a.rec + f0 + f)[w < 9 ? w : 9 + w];
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        // lane i: corner i & 3 of frame f0 + (i >> 2) (up to 8 frames)
+        // lane i: corner i & 3 of frames f0 + (i >> 2) (set A) and
+        // f0 + 8 + (i >> 2) (set B)
         const int lane = threadIdx.x;
-        const int f = f0 + (lane >> 2);
-        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
-        int cnt = 0, valid = 0;
-        if (f < f1 && s_rec[f - f0].valid) {
-            const FrameRec *r = s_rec + (f - f0);
-            const long long u = (lane & 1) ? u1 - 1 : u0;
-            const long long v = (lane & 2) ? v1 - 1 : v0;
+        int lo[2][3], hi[2][3];
+        unsigned cnt[2] = {0u, 0u}, valid[2] = {0u, 0u};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int f = (lane >> 2) + kHalfFpc * h;
 #pragma unroll
             for (int ax = 0; ax < 3; ++ax) {
-                const long long Q = r->q[6 + ax] + u * r->q[ax] + v * r->q[3 + ax];
-                lo[ax] = hi[ax] = (int)((Q + (1LL << 31)) >> 32);  // arithmetic: floor
+                lo[h][ax] = INT_MAX;
+                hi[h][ax] = INT_MIN;
             }
-            valid = 1;
-            cnt = (lane & 3) == 0 ? r->nmax : 0;
-        }
+            if (f < nf && s_rec[f].valid) {
+                const PnnRec *r = s_rec + f;
+                const long long u = (lane & 1) ? u1 - 1 : u0;
+                const long long v = (lane & 2) ? v1 - 1 : v0;
 #pragma unroll
-        for (int ax = 0; ax < 3; ++ax) {
-            lo[ax] = __reduce_min_sync(0xFFFFFFFFu, lo[ax]);
-            hi[ax] = __reduce_max_sync(0xFFFFFFFFu, hi[ax]);
-        }
-        const unsigned any = __reduce_or_sync(0xFFFFFFFFu, (unsigned)valid);
-        const unsigned nsum = __reduce_add_sync(0xFFFFFFFFu, (unsigned)cnt);
-        if (lane == 0) {
-            int mode = MODE_SKIP, check = 0, zs = 0, ex4 = 0, spill = 0;
-            // box row stride: ex rounded up to 4; plane stride 4 mod 8
-            auto strides = [](const long long (&e)[3], int &r4, long long &z) {
-                r4 = (int)((e[0] + 3) & ~3LL);
-                z = (long long)r4 * e[1];
-                z += (z & 4) ? 0 : 4;
-                return z * e[2];
-            };
-            if (any) {
-                const int n[3] = {a.nx, a.ny, a.nz};
-                mode = MODE_PACKED;
-                long long ce[3], ue[3];
-                int cl[3];
-                bool small = true;
                 for (int ax = 0; ax < 3; ++ax) {
-                    const int l = max(lo[ax], 0), h = min(hi[ax], n[ax] - 1);
-                    if (l > h)
-                        mode = MODE_SKIP;
-                    if (l != lo[ax] || h != hi[ax])
-                        check = 1;
-                    cl[ax] = l;
-                    ce[ax] = max(h - l + 1, 0);
-                    ue[ax] = (long long)hi[ax] - lo[ax] + 1;
-                    small = small && ue[ax] <= kBoxWords;
+                    const long long Q = r->q[6 + ax] + u * r->q[ax] + v * r->q[3 + ax];
+                    lo[h][ax] = hi[h][ax] = (int)((Q + (1LL << 31)) >> 32);  // arithmetic: floor
                 }
-                if (mode != MODE_SKIP && check && small && nsum <= kPackedMaxCount) {
-                    // a tile the grid clips takes its whole box if that fits:
-                    // every pixel then lands in the box with no bounds check,
-                    // and the flush drops the entries outside the grid
-                    int r4;
-                    long long z;
-                    if (strides(ue, r4, z) <= kBoxWords) {
-                        spill = 1;
-                        check = 0;
-                        ex4 = r4;
-                        zs = (int)z;
-                        for (int ax = 0; ax < 3; ++ax) {
-                            s_lo[ax] = lo[ax];
-                            s_ext[ax] = (int)ue[ax];
-                        }
-                    }
+                valid[h] = 1u;
+                cnt[h] = (lane & 3) == 0 ? (unsigned)r->nmax : 0u;
+            }
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                lo[h][ax] = __reduce_min_sync(0xFFFFFFFFu, lo[h][ax]);
+                hi[h][ax] = __reduce_max_sync(0xFFFFFFFFu, hi[h][ax]);
+            }
+            valid[h] = __reduce_or_sync(0xFFFFFFFFu, valid[h]);
+            cnt[h] = __reduce_add_sync(0xFFFFFFFFu, cnt[h]);
+        }
+        if (lane == 0) {
+            int npass = 1;
+            if (nf <= kHalfFpc) {
+                plan_box(a, lo[0], hi[0], valid[0] != 0u, cnt[0], s_plan[0]);
+            } else {
+                int wl[3], wh[3];
+                for (int ax = 0; ax < 3; ++ax) {
+                    wl[ax] = min(lo[0][ax], lo[1][ax]);
+                    wh[ax] = max(hi[0][ax], hi[1][ax]);
                 }
-                if (mode != MODE_SKIP && !spill) {
-                    for (int ax = 0; ax < 3; ++ax) {
-                        s_lo[ax] = cl[ax];
-                        s_ext[ax] = (int)ce[ax];
-                    }
-                    long long z;
-                    const long long words = strides(ce, ex4, z);
-                    zs = (int)min(z, (long long)INT_MAX);
-                    if (nsum <= kPackedMaxCount && words <= kBoxWords)
-                        mode = MODE_PACKED;
-                    else if (words <= kBoxWords / 2)
-                        mode = MODE_SPLIT;
-                    else
-                        mode = MODE_DIRECT;
+                plan_box(a, wl, wh, (valid[0] | valid[1]) != 0u, cnt[0] + cnt[1], s_plan[0]);
+                if (s_plan[0].mode != MODE_PACKED && s_plan[0].mode != MODE_SKIP) {
+                    // the group's box is too large for packed entries: two
+                    // passes of 8 frames and the rest
+                    plan_box(a, lo[0], hi[0], valid[0] != 0u, cnt[0], s_plan[0]);
+                    plan_box(a, lo[1], hi[1], valid[1] != 0u, cnt[1], s_plan[1]);
+                    npass = 2;
                 }
             }
-            s_mode = mode;
-            s_check = check;
-            s_spill = spill;
-            s_zs = zs;
-            s_ex4 = ex4;
+            s_plan[0].fa = 0;
+            s_plan[0].fb = npass == 2 ? kHalfFpc : nf;
+            s_plan[1].fa = kHalfFpc;
+            s_plan[1].fb = nf;
+            s_npass = npass;
         }
     }
-    __syncthreads();
-    const int mode = s_mode;
-    if (mode == MODE_SKIP)
-        return;
-    // each frame's Q at the tile corner (u0, v0), box-local (or global for
-    // MODE_DIRECT), with the 2^31 of the rounding folded in
-    // and at each segment's first column (u0 + 32 s); per frame whether the
-    // x and z steps are below half a voxel (the wide multiply-add loop)
-    constexpr int S = TW / kSeg;
-    for (int i = threadIdx.x; i < 3 * S * (f1 - f0); i += kThreads) {
-        const int fi = i / (3 * S), sg = (i / 3) % S, ax = i % 3;
-        const FrameRec *r = s_rec + fi;
-        const long long off =
-            (1LL << 31) - (mode == MODE_DIRECT ? 0LL : (long long)s_lo[ax] * (1LL << 32));
-        s_q0[fi][sg][ax] = r->q[6 + ax] + (long long)(u0 + kSeg * sg) * r->q[ax] +
-                           (long long)v0 * r->q[3 + ax] + off;
-    }
-    if (threadIdx.x < f1 - f0) {
+    // per frame whether the x and z steps are below half a voxel (the wide
+    // multiply-add loop)
+    if (threadIdx.x < nf) {
         const long long Ax = s_rec[threadIdx.x].q[0], Az = s_rec[threadIdx.x].q[2];
         s_narrow[threadIdx.x] = Ax > -(1LL << 31) && Ax < (1LL << 31) &&
                                 Az > -(1LL << 31) && Az < (1LL << 31);
     }
-    if (mode == MODE_DIRECT) {
+    __syncthreads();
+    const int npass = s_npass;
+    for (int ps = 0; ps < npass; ++ps) {
+        const Plan &P = s_plan[ps];
+        const int mode = P.mode, fa = P.fa, fb = P.fb;
+        if (mode == MODE_SKIP)
+            continue;
+        // each frame's Q at each segment's first column (u0 + 32 s) of the
+        // tile's first row, box-local (or global for MODE_DIRECT), with the
+        // 2^31 of the rounding folded in
+        for (int i = threadIdx.x; i < 3 * S * (fb - fa); i += kThreads) {
+            const int fi = fa + i / (3 * S), sg = (i / 3) % S, ax = i % 3;
+            const PnnRec *r = s_rec + fi;
+            const long long off =
+                (1LL << 31) - (mode == MODE_DIRECT ? 0LL : (long long)P.lo[ax] * (1LL << 32));
+            s_q0[fi][sg][ax] = r->q[6 + ax] + (long long)(u0 + kSeg * sg) * r->q[ax] +
+                               (long long)v0 * r->q[3 + ax] + off;
+        }
+        if (mode == MODE_DIRECT) {
+            __syncthreads();
+            // keys are global linear indices into the whole grid
+            const Box g = {(unsigned)a.nx, (unsigned)a.ny, (unsigned)a.nz,
+                           (unsigned)a.nx * (unsigned)a.ny, (unsigned)a.nx,
+                           (unsigned long long)a.nx * a.ny * a.nz, a.status};
+            run_tile<TW, VEC, true, MODE_DIRECT>(a, f0, fa, fb, u0, u1, v0, v1, g, nullptr, 0,
+                                                 s_rec, s_q0, s_narrow);
+            if (ps + 1 < npass)
+                __syncthreads();
+            continue;
+        }
+        const Box bx = {(unsigned)P.ext[0], (unsigned)P.ext[1], (unsigned)P.ext[2], (unsigned)P.zs,
+                        (unsigned)P.ex4, (unsigned long long)(unsigned)P.zs * (unsigned)P.ext[2],
+                        a.status};
+        const unsigned bwords = bx.zs * bx.ez;
+        const unsigned cap = kBoxWords / 2;
+        {
+            // 16-byte stores (every stride is a multiple of 4 words)
+            const unsigned quads = bwords / 4;
+            uint4 *b4 = reinterpret_cast<uint4 *>(box);
+            for (unsigned i = threadIdx.x; i < quads; i += kThreads) {
+                b4[i] = make_uint4(0u, 0u, 0u, 0u);
+                if (mode == MODE_SPLIT)
+                    b4[cap / 4 + i] = make_uint4(0u, 0u, 0u, 0u);
+            }
+        }
         __syncthreads();
-        // keys are global linear indices into the whole grid
-        const Box g = {(unsigned)a.nx, (unsigned)a.ny, (unsigned)a.nz,
-                       (unsigned)a.nx * (unsigned)a.ny, (unsigned)a.nx,
-                       (unsigned long long)a.nx * a.ny * a.nz, a.status};
-        run_tile<TW, VEC, true, MODE_DIRECT>(a, f0, f1, u0, u1, v0, v1, g, nullptr, 0, s_rec,
-                                             s_q0, s_narrow);
-        return;
-    }
-    const Box bx = {(unsigned)s_ext[0], (unsigned)s_ext[1], (unsigned)s_ext[2], (unsigned)s_zs,
-                    (unsigned)s_ex4,
-                    (unsigned long long)(unsigned)s_zs * (unsigned)s_ext[2], a.status};
-    const unsigned bwords = bx.zs * bx.ez;
-    const unsigned cap = kBoxWords / 2;
-    {
-        // 16-byte stores (every stride is a multiple of 4 words)
-        const unsigned quads = bwords / 4;
-        uint4 *b4 = reinterpret_cast<uint4 *>(box);
-        for (unsigned i = threadIdx.x; i < quads; i += kThreads) {
-            b4[i] = make_uint4(0u, 0u, 0u, 0u);
-            if (mode == MODE_SPLIT)
-                b4[cap / 4 + i] = make_uint4(0u, 0u, 0u, 0u);
+        if (mode == MODE_PACKED) {
+            if (P.check)
+                run_tile<TW, VEC, true, MODE_PACKED>(a, f0, fa, fb, u0, u1, v0, v1, bx, box,
+                                                     0, s_rec, s_q0, s_narrow);
+            else
+                run_tile<TW, VEC, false, MODE_PACKED>(a, f0, fa, fb, u0, u1, v0, v1, bx, box,
+                                                     0, s_rec, s_q0, s_narrow);
+        } else {
+            if (P.check)
+                run_tile<TW, VEC, true, MODE_SPLIT>(a, f0, fa, fb, u0, u1, v0, v1, bx, box,
+                                                     cap, s_rec, s_q0, s_narrow);
+            else
+                run_tile<TW, VEC, false, MODE_SPLIT>(a, f0, fa, fb, u0, u1, v0, v1, bx, box,
+                                                     cap, s_rec, s_q0, s_narrow);
         }
-    }
-    __syncthreads();
-    if (mode == MODE_PACKED) {
-        if (s_check)
-            run_tile<TW, VEC, true, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, bx, box, 0, s_rec,
-                                                 s_q0, s_narrow);
-        else
-            run_tile<TW, VEC, false, MODE_PACKED>(a, f0, f1, u0, u1, v0, v1, bx, box, 0, s_rec,
-                                                  s_q0, s_narrow);
-    } else {
-        if (s_check)
-            run_tile<TW, VEC, true, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, bx, box, cap, s_rec,
-                                                s_q0, s_narrow);
-        else
-            run_tile<TW, VEC, false, MODE_SPLIT>(a, f0, f1, u0, u1, v0, v1, bx, box, cap, s_rec,
-                                                 s_q0, s_narrow);
-    }
-    __syncthreads();
-    // Flush: the threads take the box's quads (4 consecutive x entries of one
-    // (y, z) row) in row order; quad p is row p / qr, quad p % qr of it, the
-    // row (y, z) = (row % ey, row / ey), both by exact multiply-high
-    // division.  Each touched entry goes to HBM with one packed 64-bit
-    // atomic; the x padding of a row is never touched, so it is skipped as
-    // empty.  The whole box of a clipped tile (spill) may hold entries
-    // outside the grid: they are dropped here, by row and by entry.
-    {
-        const unsigned qr = bx.ex4 / 4, nq = qr * bx.ey * bx.ez;
-        const unsigned mq = div_magic(qr), my = div_magic(bx.ey);
-        const long long gplane = (long long)a.nx * a.ny;
-        const bool spill = s_spill != 0;
-        // signed: a spilled box may start before the grid
-        const long long gbase = ((long long)s_lo[2] * a.ny + s_lo[1]) * a.nx + s_lo[0];
-        const unsigned long long nvox = (unsigned long long)a.nx * a.ny * a.nz;
-        for (unsigned p = threadIdx.x; p < nq; p += kThreads) {
-            const unsigned row = div_by(p, qr, mq), qx4 = 4u * (p - row * qr);
-            const unsigned lz = div_by(row, bx.ey, my), ly = row - lz * bx.ey;
-            const unsigned off = lz * bx.zs + ly * bx.ex4 + qx4;
-            const uint4 e = *reinterpret_cast<const uint4 *>(box + off);
-            uint4 c4 = e;
-            if (mode != MODE_PACKED)
-                c4 = *reinterpret_cast<const uint4 *>(box + cap + off);
-            if ((e.x | e.y | e.z | e.w | c4.x | c4.y | c4.z | c4.w) == 0u)
-                continue;
-            unsigned xin = 0xFu;  // entries of the quad inside the grid
-            if (spill) {
-                if ((unsigned)(s_lo[1] + (int)ly) >= (unsigned)a.ny ||
-                    (unsigned)(s_lo[2] + (int)lz) >= (unsigned)a.nz)
-                    continue;
-                const int gx = s_lo[0] + (int)qx4;
-                xin = 0u;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    xin |= ((unsigned)(gx + k) < (unsigned)a.nx ? 1u : 0u) << k;
-            }
-            const long long gi = gbase + (long long)lz * gplane + (long long)ly * a.nx + qx4;
-            const unsigned ev[4] = {e.x, e.y, e.z, e.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                unsigned sv, cn;
-                if (mode == MODE_PACKED) {
-                    sv = ev[k] & ((1u << kCountShift) - 1);
-                    cn = ev[k] >> kCountShift;
-                } else {
-                    sv = ev[k];
-                    cn = cv[k];
-                }
-                if (cn != 0u && ((xin >> k) & 1u) && guard(qx4 + k, bx.ex, a.status) &&
-                    guard((unsigned long long)(gi + k), nvox, a.status))
-                    atomicAdd(a.acc + (gi + k), pack64(sv, cn));
-            }
+        __syncthreads();
+        // Flush: the threads take the box's quads (4 consecutive x entries of
+        // one (y, z) row) in row order; each touched entry goes to HBM with
+        // one packed 64-bit atomic (flush_box).
+        if (mode == MODE_PACKED) {
+            if (P.spill)
+                flush_box<MODE_PACKED, true>(a, box, cap, bx, P.lo);
+            else
+                flush_box<MODE_PACKED, false>(a, box, cap, bx, P.lo);
+        } else {
+            flush_box<MODE_SPLIT, false>(a, box, cap, bx, P.lo);
         }
+        if (ps + 1 < npass)
+            __syncthreads();  // the next pass clears the box
     }
 }
 
@@ -708,7 +805,8 @@ cudaError_t launch_tw(const PnnArgs &a, dim3 grid, bool vec, cudaStream_t st)
 bool pnn_tile_ok(const TileCfg &c)
 {
     return (c.tile_w == 64 || c.tile_w == 128 || c.tile_w == 256) && c.tile_h >= 1 &&
-           c.tile_h <= 1024 && c.frames_per_cta >= 1 && c.frames_per_cta <= kMaxFpc;
+           c.tile_h <= 1024 && c.frames_per_cta >= 1 &&
+           c.frames_per_cta <= (c.tile_w == 256 ? kHalfFpc : kMaxFpc);
 }
 
 namespace {

@@ -832,12 +832,13 @@ int tune_candidates(int mode, TileCfg *out)
     int k = 0;
     if (mode == USV_PNN) {
         out[k++] = kPnnTileDefault;
-        const int tw[3] = {64, 128, 256}, th[5] = {32, 48, 64, 96, 128}, fpc[3] = {4, 6, 8};
+        const int tw[3] = {64, 128, 256}, th[5] = {32, 48, 64, 96, 128}, fpc[4] = {4, 8, 12, 16};
         for (int a : tw)
             for (int b : th)
                 for (int c : fpc) {
                     const TileCfg t{a, b, c};
-                    if (!(a == kPnnTileDefault.tile_w && b == kPnnTileDefault.tile_h &&
+                    if (pnn_tile_ok(t) &&
+                        !(a == kPnnTileDefault.tile_w && b == kPnnTileDefault.tile_h &&
                           c == kPnnTileDefault.frames_per_cta))
                         out[k++] = t;
                 }
@@ -893,7 +894,7 @@ int usv_tune_insert(usv_volume *vol, const void *images_dev, int32_t n, int32_t 
     const size_t acc_bytes = (size_t)v.g.nx * v.g.ny * v.g.nz * 8;
     if (scratch_bytes < acc_bytes)
         return USV_ERR_NOMEM;
-    const int nt = n < 1024 ? n : 1024;
+    const int nt = n < 4096 ? n : 4096;
     usv::TileCfg cand[64];
     const int ncand = usv::tune_candidates(v.mode, cand);
     usv::DeviceGuard g(v.device);

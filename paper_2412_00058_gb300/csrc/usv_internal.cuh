@@ -45,7 +45,7 @@ static_assert(sizeof(FrameRec) == 160, "FrameRec layout");
 using TileCfg = usv_tile_config;
 // Defaults, from the whole-spine profiles: PNN 128 x 64 pixels x 8 frames,
 // trilinear 256 columns x 64 rows x 4 frames.
-constexpr TileCfg kPnnTileDefault = {128, 64, 8};
+constexpr TileCfg kPnnTileDefault = {128, 64, 12};
 constexpr TileCfg kTriTileDefault = {256, 64, 4};
 constexpr int kTunedCap = 8;  // frame sizes (H, W) with a chosen tile per volume
 

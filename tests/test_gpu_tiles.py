@@ -55,8 +55,9 @@ def run_with_tile(w, cfg, tune=False):
 
 
 PNN_SHAPES = [(tw, th, f) for tw in (64, 128, 256) for th in (32, 48, 64, 96, 128)
-              for f in (4, 6, 8)]
-PNN_SHAPES += [(128, 7, 3), (64, 1, 1), (256, 200, 8), (64, 640, 2)]
+              for f in (4, 8, 12, 16) if tw < 256 or f <= 8]
+PNN_SHAPES += [(128, 7, 3), (64, 1, 1), (256, 200, 8), (64, 640, 2), (128, 64, 6),
+               (128, 64, 11), (64, 5, 13)]
 
 
 def test_every_pnn_tile_shape_bit_exact():
@@ -67,6 +68,23 @@ def test_every_pnn_tile_shape_bit_exact():
     w = synth.whole_spine(n=21, grid=(270, 60, 200), y_start_mm=3.0, y_span_mm=8.0)
     o = oracle_run(w)
     for cfg in PNN_SHAPES:
+        g = run_with_tile(w, cfg)
+        assert g["status"] == 0
+        assert_pnn_bit_exact(g, o)
+
+
+@pytest.mark.parametrize("span_mm", [8.0, 14.0])
+def test_pnn_two_pass_groups_bit_exact(span_mm):
+    """Frames about one voxel apart (14 mm over 48 frames) make the box of
+    12 or 16 frames too large for packed shared-memory entries in most
+    tiles, so those blocks insert their group as two passes (the first 8
+    frames, then the rest), and a few blocks' halves still do not fit and
+    take the two-word or direct modes; 8 mm over 48 frames mixes one- and
+    two-pass blocks.  Every shape stays bit-exact."""
+    from paper_2412_00058_gb300 import synth
+    w = synth.whole_spine(n=48, grid=(270, 90, 200), y_start_mm=3.0, y_span_mm=span_mm)
+    o = oracle_run(w)
+    for cfg in [(128, 64, 16), (128, 64, 12), (128, 64, 11), (64, 32, 16), (128, 64, 8)]:
         g = run_with_tile(w, cfg)
         assert g["status"] == 0
         assert_pnn_bit_exact(g, o)
@@ -91,7 +109,7 @@ def test_autotuner_pnn_keeps_a_valid_shape_and_stays_exact():
     assert_pnn_bit_exact(g, oracle_run(w))
     vol = g["vol"]
     vol.set_tile(640, 480, None)  # back to the default
-    assert vol.get_tile(640, 480) == (128, 64, 8)
+    assert vol.get_tile(640, 480) == (128, 64, 12)
 
 
 def test_tile_config_errors():
@@ -99,7 +117,8 @@ def test_tile_config_errors():
     from paper_2412_00058_gb300 import synth, usvol
     w = synth.tiny_pnn(n=4, H=32, W=32, grid=(40, 40, 40))
     vol = usvol.Volume(w.grid, w.spacing, w.origin, "pnn")
-    for bad in [(96, 64, 8), (128, 0, 8), (128, 64, 9), (128, 2000, 1), (128, 64, 0)]:
+    for bad in [(96, 64, 8), (128, 0, 8), (128, 64, 17), (256, 64, 9), (128, 2000, 1),
+                (128, 64, 0)]:
         with pytest.raises(usvol.UsvError) as e:
             vol.set_tile(32, 32, bad)
         assert e.value.code == usvol.ERR_RANGE
