@@ -450,13 +450,6 @@ __device__ __forceinline__ void flush_box(const PnnArgs &a, const unsigned *box,
     // signed: a spilled box may start before the grid
     const long long gbase = ((long long)lo[2] * a.ny + lo[1]) * a.nx + lo[0];
     const unsigned long long nvox = (unsigned long long)a.nx * a.ny * a.nz;
-#ifdef USV_FL32
-    // the box's span in the grid, in entries, fits 32 bits: offsets from the
-    // box's first entry are 32-bit
-    const bool n32 = (unsigned long long)bx.ez * (unsigned long long)gplane < (1ull << 32);
-    const unsigned gp32 = (unsigned)gplane, nx32 = (unsigned)a.nx;
-    unsigned long long *const gb = a.acc + gbase;
-#endif
     for (unsigned p = threadIdx.x; p < nq; p += kThreads) {
         const unsigned row = div_by(p, qr, mq), qx4 = 4u * (p - row * qr);
         const unsigned lz = div_by(row, bx.ey, my), ly = row - lz * bx.ey;
@@ -482,11 +475,7 @@ __device__ __forceinline__ void flush_box(const PnnArgs &a, const unsigned *box,
                 xin |= ((unsigned)(gx + k) < (unsigned)a.nx ? 1u : 0u) << k;
         }
         const long long gi = gbase + (long long)lz * gplane + (long long)ly * a.nx + qx4;
-        unsigned long long *g = a.acc + gi;
-#ifdef USV_FL32
-        if (!kChecked && n32)
-            g = gb + (lz * gp32 + ly * nx32 + qx4);
-#endif
+        unsigned long long *const g = a.acc + gi;
         const unsigned ev[4] = {e.x, e.y, e.z, e.w}, cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
