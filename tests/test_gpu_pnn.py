@@ -180,6 +180,50 @@ def test_fill_and_projection_on_hand_built_accumulators():
         assert np.array_equal(vol.read(usvol.READ_MASK).cpu().numpy(), oh)
 
 
+def test_projection_word_kernel_grids_and_pointer_alignments():
+    """Whole-plane projections take 4 columns per thread where the plane
+    allows 32-bit words; grids whose 4-column groups wrap rows (nx not a
+    multiple of 4), cross 32-column mask words, or would span three mask
+    words (nx = 1 or 2 mod 32, taken by the one-column kernel), and outputs
+    at 16-byte, 4-byte and 2-byte alignments, with and without counts, all
+    equal the oracle."""
+    import torch
+    import oracle
+    from paper_2412_00058_gb300 import usvol
+    rng = np.random.default_rng(77)
+    for grid in [(270, 12, 20), (45, 4, 9), (63, 4, 9), (31, 4, 5), (33, 4, 6), (66, 2, 6),
+                 (36, 5, 12), (45, 3, 4)]:
+        nx, ny, nz = grid
+        c = np.where(rng.random((nz, ny, nx)) < 0.3, rng.integers(1, 50, (nz, ny, nx)), 0)
+        s = (c * rng.integers(0, 256, (nz, ny, nx))).astype(np.uint64)
+        c = c.astype(np.uint32)
+        packed = (c.astype(np.uint64) << np.uint64(32)) | s
+        vol = usvol.Volume(grid, (0.5, 0.5, 0.5), (0, 0, 0), "pnn")
+        src = torch.from_numpy(packed.view(np.int64)).cuda()
+        usvol.volume_write_accum(vol.handle, src.data_ptr())
+        vol.fill()
+        ov, oh = oracle.fill_pnn(s, c)
+        n = nx * ny
+        for lo, hi in [(0, nz), (1, nz), (nz - 1, nz)]:
+            op, oc = oracle.project_u8(ov, oh, lo, hi)
+            for off_out, off_cnt, with_cnt in [(0, 0, True), (1, 1, True), (4, 4, True),
+                                               (0, 0, False), (1, 0, False)]:
+                out = torch.full((n + 8,), -1.0, dtype=torch.float32, device="cuda")
+                cnt = torch.full((n + 8,), 7, dtype=torch.int16, device="cuda")
+                usvol.project_depth_band(vol.handle, lo, hi, out.data_ptr() + 4 * off_out,
+                                         cnt.data_ptr() + 2 * off_cnt if with_cnt else None)
+                torch.cuda.synchronize()
+                o = out.cpu().numpy()
+                assert np.array_equal(o[off_out:off_out + n].reshape(ny, nx), op), (grid, lo, off_out)
+                assert (o[:off_out] == -1.0).all() and (o[off_out + n:] == -1.0).all()
+                k = cnt.cpu().numpy().view(np.uint16)
+                if with_cnt:
+                    assert np.array_equal(k[off_cnt:off_cnt + n].reshape(ny, nx), oc)
+                    assert (k[:off_cnt] == 7).all() and (k[off_cnt + n:] == 7).all()
+                else:
+                    assert (k == 7).all()
+
+
 def test_fill_large_accumulators_both_plane_loaders():
     """Counts at and above 2^24 (the fill's 64-bit path and the saturation
     flag) next to ordinary planes, on an even nx (planes arrive by tensor
