@@ -343,7 +343,9 @@ __device__ __forceinline__ void load_segment(const uint8_t *p, int npx, uint4 &w
     }
 }
 
-// All of the CTA's segments of all its frames, in one box mode.
+// All of the CTA's segments of the frames f0 + ga .. f0 + gb - 1 (one pass
+// of its group; recs, q0 and narrowf are indexed from the group's first
+// frame), in one box mode.
 template <int TW, bool VEC, bool CHECK, int MODE>
 __device__ __forceinline__ void run_tile(const PnnArgs &a, int f0, int ga, int gb, int u0, int u1,
                                          int v0, int v1, const Box &bx, unsigned *box,
