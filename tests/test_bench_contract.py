@@ -97,3 +97,27 @@ def test_gpu_arm_line():
     assert d["cuda_graph"]["ms_per_step"] > 0 and d["autotune"]["tile"]
     clocks = d["clocks"]
     assert clocks is None or "sm_mhz" in clocks
+
+
+def test_kernel_record_is_used_only_for_its_own_source(tmp_path):
+    """roofline.traffic and the issue roofline come from the committed ncu
+    record of the insertion kernel only while the kernel source still has the
+    record's sha256; a record of another source gives nothing."""
+    import hashlib
+    sys.path.insert(0, ROOT)
+    import bench
+    kernel = tmp_path / "k.cu"
+    kernel.write_text("// a kernel\n")
+    sha = hashlib.sha256(kernel.read_bytes()).hexdigest()
+    rec = tmp_path / "rec.txt"
+    body = ("# comment = ignored\nkernel = k\nsource_sha256 = {}\n"
+            "dram_bytes_read = 1.5e9\ndram_bytes_write = 0.5e9\nwarp_inst_per_pixel = 0.5\n")
+    rec.write_text(body.format(sha))
+    kv = bench.insert_record(str(kernel), str(rec))
+    assert float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"]) == 2.0e9
+    assert kv["warp_inst_per_pixel"] == "0.5" and "comment" not in kv
+    rec.write_text(body.format("0" * 64))
+    assert bench.insert_record(str(kernel), str(rec)) == {}
+    kernel.write_text("// a kernel, changed\n")
+    rec.write_text(body.format(sha))
+    assert bench.insert_record(str(kernel), str(rec)) == {}
